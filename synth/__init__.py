@@ -1,0 +1,125 @@
+"""Seeded synthetic inputs shared by the oracle, the tests and the benchmark.
+
+This module holds no arithmetic of the simulation method itself: it only
+builds the inputs a user would supply -- unit vectors of sky pixels, a target
+angular power spectrum C_l, and the named workloads.  Both the FP64 oracle and
+the CUDA path receive exactly these arrays.
+
+Pixels.  The paper samples the box at HEALPix pixels, taking the first pixels of
+a RING-ordered map as the polar cap (Sec. II.D.1).  HEALPix is not available
+here, so an equal-area Fibonacci grid stands in for it: point i of Npix has
+z_i = 1 - (2i+1)/Npix and azimuth 2*pi*frac(i*(sqrt(5)-1)/2).  Like RING order,
+index order runs from the north pole southwards, so a polar cap of sky fraction
+f_sky is the first round(f_sky*Npix) points.
+
+Spectrum.  The target C_l family is
+    C_l = A / (l(l+1)) * (1 + 0.5 cos(pi*l/p)) * exp(-(l/d)^2),
+an l(l+1)-flat spectrum with an oscillation of period p (standing in for
+acoustic peaks) and a Gaussian beam, which is the smoothing of Eq. (2.2) with
+b = 1/d.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+GOLDEN_FRACTION = (math.sqrt(5.0) - 1.0) / 2.0
+
+
+def fibonacci_sphere(npix: int, count: int | None = None) -> np.ndarray:
+    """Unit vectors (count x 3, float64) of the first `count` points of an
+    equal-area Fibonacci grid of `npix` points, ordered from the north pole."""
+    if count is None:
+        count = npix
+    i = np.arange(count, dtype=np.float64)
+    z = 1.0 - (2.0 * i + 1.0) / npix
+    frac = np.mod(i * GOLDEN_FRACTION, 1.0)
+    phi = 2.0 * np.pi * frac
+    s = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    out = np.empty((count, 3), dtype=np.float64)
+    out[:, 0] = s * np.cos(phi)
+    out[:, 1] = s * np.sin(phi)
+    out[:, 2] = z
+    return out
+
+
+def cap_count(npix: int, fsky: float) -> int:
+    """Number of grid points with z >= 1 - 2 f_sky (a polar cap of area
+    fraction f_sky): the first floor(f_sky*npix + 1/2) indices."""
+    return int(math.floor(fsky * npix + 0.5))
+
+
+def cap_pixels(nside: int, fsky: float) -> np.ndarray:
+    """Polar-cap pixels of a 12*nside^2-point Fibonacci grid."""
+    npix = 12 * nside * nside
+    return fibonacci_sphere(npix, cap_count(npix, fsky))
+
+
+def cl_family(lmax: int, amplitude: float = 1e3, period: float = 22.0,
+              damping: float = 100.0, lmin: int = 2) -> tuple[np.ndarray, np.ndarray]:
+    """(l, C_l) for l = lmin..lmax of the synthetic spectrum family."""
+    ell = np.arange(lmin, lmax + 1, dtype=np.float64)
+    cl = (amplitude / (ell * (ell + 1.0)) * (1.0 + 0.5 * np.cos(np.pi * ell / period))
+          * np.exp(-(ell / damping) ** 2))
+    return ell, cl
+
+
+def random_cl_family(rng: np.random.Generator, n: int, lmax: int,
+                     amp_range=(1e2, 1e4), period_range=(15.0, 30.0),
+                     damping_range=(800.0, 2000.0)) -> tuple[np.ndarray, np.ndarray]:
+    """n spectra of the family with log-uniform amplitude and uniform period
+    and damping, drawn from `rng`.  Returns (ell, cl[n, len(ell)])."""
+    amp = np.exp(rng.uniform(math.log(amp_range[0]), math.log(amp_range[1]), n))
+    per = rng.uniform(*period_range, n)
+    dmp = rng.uniform(*damping_range, n)
+    ell = np.arange(2, lmax + 1, dtype=np.float64)
+    cl = (amp[:, None] / (ell * (ell + 1.0)) * (1.0 + 0.5 * np.cos(np.pi * ell[None, :] / per[:, None]))
+          * np.exp(-(ell[None, :] / dmp[:, None]) ** 2))
+    return ell, cl
+
+
+def batch_fsky(nbox: int, seed: int = 2507, lo: float = 0.05, hi: float = 0.5) -> np.ndarray:
+    """Per-box sky fractions of the batched workload, uniform on [lo, hi]."""
+    return np.random.default_rng(seed).uniform(lo, hi, nbox)
+
+
+@dataclasses.dataclass(frozen=True)
+class Workload:
+    """A named synthetic workload: box, spectrum, pixels and interpolation."""
+    name: str
+    N: int                  # box points per axis
+    nside: int              # pixel grid has 12*nside^2 points on the full sphere
+    fsky: float             # polar-cap sky fraction sampled
+    lmax: int               # C_l given for l = 2..lmax
+    damping: float          # d in exp(-(l/d)^2)
+    interp: int             # 1 = trilinear, 3 = tricubic
+    nkbins: int = 256       # k nodes of the fitted P(k)
+    r: float = 1.0          # sphere radius
+    L_over_r: float = 2.2   # box side in units of r
+    amplitude: float = 1e3
+    period: float = 22.0
+
+    @property
+    def L(self) -> float:
+        return self.L_over_r * self.r
+
+    def pixels(self) -> np.ndarray:
+        return cap_pixels(self.nside, self.fsky)
+
+    def cl(self) -> tuple[np.ndarray, np.ndarray]:
+        return cl_family(self.lmax, self.amplitude, self.period, self.damping)
+
+
+WORKLOADS = {
+    # 64^3 box, ~1.2k cap pixels, trilinear: the small parity workload.
+    "box64_cap0.1_trilinear": Workload("box64_cap0.1_trilinear", N=64, nside=32, fsky=0.1,
+                                       lmax=128, damping=100.0, interp=1),
+    # 512^3 box, ~5M cap pixels, tricubic: the single-realization production workload.
+    "box512_cap0.4_tricubic": Workload("box512_cap0.4_tricubic", N=512, nside=1024, fsky=0.4,
+                                       lmax=768, damping=600.0, interp=3),
+    # 1024^3 box, ~20M cap pixels, tricubic.
+    "box1024_cap0.4_tricubic": Workload("box1024_cap0.4_tricubic", N=1024, nside=2048, fsky=0.4,
+                                        lmax=768, damping=600.0, interp=3),
+}
