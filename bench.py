@@ -1,0 +1,370 @@
+"""Benchmark: partial-sky maps per second on the GB300 (3-D Fourier method).
+
+One step = one complete map of the workload through the C ABI: Philox draw
+fused with the z-FFT, y-FFT, x complex-to-real FFT and the tricubic gather at
+the cap pixels.  Default workload: a 512^3 box (L = 2.2 r) sampled at the
+5,033,165 pixels of an f_sky = 0.4 polar cap of a 12*1024^2-point grid.
+
+The line printed by rank 0 carries maps/s (device-timed, inputs resident),
+the end-to-end figure through the host-buffer entry point, the roofline of
+the dominant kernel (algorithmic bytes / its CUDA-event time), the FP64
+oracle timed on the host cores, clocks sampled during the timed region and
+the number of kernel launches.
+
+--impl reference runs the FP64 oracle on the host cores instead (the only
+other place this script executes the oracle).
+
+Multi-GPU: independent replicas (one process per GPU, seeds offset by rank),
+no data-path collective; the timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from synth import WORKLOADS  # noqa: E402
+
+DEFAULT_WORKLOAD = "box512_cap0.4_tricubic"
+METRIC = "partial-sky maps/sec and achieved HBM GB/s at N^3 box, Npix pixels, 1 GB300"
+L2_BYTES = 129 * 2 ** 20
+
+
+# --------------------------------------------------------------------------
+# helpers
+# --------------------------------------------------------------------------
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+
+        def pump():
+            for line in self.proc.stdout:
+                self.lines.append(line.strip())
+        self.thread = threading.Thread(target=pump, daemon=True)
+        self.thread.start()
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+def source_hash(files):
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+KERNEL_SOURCES = {
+    "draw_zfft": ["paper_2507_15703_gb300/csrc/fft_passes.cu", "paper_2507_15703_gb300/csrc/device_common.cuh"],
+    "yfft": ["paper_2507_15703_gb300/csrc/fft_passes.cu", "paper_2507_15703_gb300/csrc/device_common.cuh"],
+    "xc2r": ["paper_2507_15703_gb300/csrc/fft_passes.cu", "paper_2507_15703_gb300/csrc/device_common.cuh"],
+    "gather": ["paper_2507_15703_gb300/csrc/gather.cu"],
+}
+
+
+def ncu_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, or None when the
+    kernel source changed since the counters were taken."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(workload, {}).get(kernel)
+    if not e or e.get("source_hash") != source_hash(KERNEL_SOURCES[kernel]):
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def algorithmic_bytes(N: int, npix: int) -> dict:
+    """Bytes each kernel must move per launch (the packed half spectrum and the
+    real field are both 4 N^3 bytes): draw_zfft writes it once; yfft and xc2r
+    read and write it once; gather reads 16 B of table + 4 B of permutation per
+    pixel and writes 4 B per pixel (field reads are cache-dependent and not
+    counted)."""
+    box = 4 * N ** 3
+    return {"draw_zfft": box, "yfft": 2 * box, "xc2r": 2 * box, "gather": 24 * npix}
+
+
+# --------------------------------------------------------------------------
+# the CUDA arm
+# --------------------------------------------------------------------------
+
+def run_cuda(args, rank, world, local):
+    import torch
+    from paper_2507_15703_gb300 import cmb3d
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = WORKLOADS[args.workload]
+    pix = w.pixels()
+    npix = pix.shape[0]
+    ell, cl = w.cl()
+
+    t0 = time.time()
+    plan = cmb3d.Plan(w.N, w.L, w.r, pix, w.interp, cmb3d.CMB3D_FLAG_STAGE_TIMING)
+    fit_err = plan.set_cl(ell, cl, w.nkbins)
+    setup_s = time.time() - t0
+    stream = torch.cuda.current_stream(dev)
+    out = torch.empty(npix, dtype=torch.float32, device=dev)
+    seed0 = 1000003 * rank
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for i in range(args.warmup):
+        plan.realize_sample(seed0 + i, out, stream)
+    torch.cuda.synchronize(dev)
+    cmb3d.cmb3d_stage_times(plan.handle, reset=True)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for i in range(args.steps):
+        plan.realize_sample(seed0 + args.warmup + i, out, stream)
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    stage_ms, stage_n = cmb3d.cmb3d_stage_times(plan.handle, reset=True)
+
+    t_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+
+    # end to end through the host-buffer entry point (map copied to pinned host memory)
+    host = torch.empty(npix, dtype=torch.float32).pin_memory().numpy()
+    cmb3d.cmb3d_realize_sample_to_host(plan.handle, seed0, host, stream)
+    barrier()
+    t1 = time.perf_counter()
+    for i in range(args.steps):
+        cmb3d.cmb3d_realize_sample_to_host(plan.handle, seed0 + i, host, stream)
+    barrier()
+    e2e_s = time.perf_counter() - t1
+    if dist is not None:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    cmb3d.cmb3d_stage_times(plan.handle, reset=True)
+    plan.close()
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    maps = world * args.steps
+    value = maps / (t_max / 1e3)
+    ab = algorithmic_bytes(w.N, npix)
+    names = cmb3d.STAGE_NAMES
+    peak, peak_kind = measured_peaks()
+    kernels = {}
+    for i, name in enumerate(names):
+        n = int(stage_n[i])
+        avg_ms = stage_ms[i] / max(n, 1)
+        gbs = ab[name] / (avg_ms / 1e3) / 1e9 if n else None
+        kernels[name] = {"launches": n, "avg_ms": round(avg_ms, 5), "share": round(stage_ms[i] / max(stage_ms.sum(), 1e-12), 4),
+                         "alg_bytes": ab[name], "alg_gbs": round(gbs, 1) if gbs else None,
+                         "frac_of_measured_hbm": round(gbs / peak, 4) if gbs else None}
+    dom = names[int(np.argmax(stage_ms))]
+    dk = kernels[dom]
+    per_map_bytes = sum(ab.values())
+    line = {
+        "metric": METRIC,
+        "value": round(value, 3),
+        "unit": "maps/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(t_max / args.steps, 5),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic: Fibonacci-grid polar cap pixels, C_l family inverted to P(k) by the library's NNLS",
+        "config": {"workload": args.workload, "N": w.N, "L_over_r": w.L_over_r, "npix": npix, "fsky": w.fsky,
+                   "interp": "tricubic" if w.interp == 3 else "trilinear", "lmax": w.lmax, "nkbins": w.nkbins,
+                   "parallelism": f"replicas x{world}",
+                   "l2": f"no flush: per-map working set {per_map_bytes / 2**30:.2f} GiB > 129 MiB L2",
+                   "cl_fit_max_rel_err": fit_err, "plan_setup_s": round(setup_s, 2)},
+        "achieved_gbs_alg_per_map": round(per_map_bytes * value / world / 1e9, 1),
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": dk["alg_gbs"], "peak": peak, "unit": "GB/s",
+                     "frac": dk["frac_of_measured_hbm"], "peak_source": peak_kind,
+                     "traffic": ncu_traffic(dom, args.workload)},
+        "kernels": kernels,
+        "e2e": {"value": round(maps / e2e_s, 3), "unit": "maps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 4 * npix},
+        "gpu_launches": int(stage_n.sum()),
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, args)
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# --------------------------------------------------------------------------
+# the oracle on the host cores
+# --------------------------------------------------------------------------
+
+def oracle_map_sample(w, seed):
+    """One map of the workload computed by the FP64 oracle (draw, inverse FFT,
+    interpolation at every pixel).  Returns (seconds, pixels done)."""
+    from oracle import cmb3d_oracle as orc
+    k = np.linspace(0.0, math.sqrt(3) * math.pi * w.N / w.L, w.nkbins)
+    pk = 1e-3 / (1.0 + (k / 12.0) ** 3)
+    pb = orc.p_box_of_q(w.N, w.L, k, pk)
+    pix = w.pixels()
+    t = time.perf_counter()
+    vals = orc.realize_sample(w.N, w.L, w.r, pix, pb, seed, w.interp)
+    return time.perf_counter() - t, vals.size
+
+
+def cpu_baseline(w, args):
+    """The oracle, as it stands, timed on one full map of the same workload on
+    the host cores (numpy FP64; one map is the bounded sample)."""
+    threads = os.cpu_count()
+    secs, _ = oracle_map_sample(w, 0)
+    return {"value": round(1.0 / secs, 6), "unit": "maps/s", "cores": threads, "kind": "oracle",
+            "sample": f"one full map of {args.workload} by the numpy FP64 oracle ({secs:.1f} s)"}
+
+
+def run_reference(args, rank, world):
+    """The oracle arm: full maps of the workload by the FP64 oracle on the host
+    cores.  Each step is one map; the run stops early once --ref-budget-s of
+    timed work is spent (at least one warm-up and one timed map), and the line
+    reports the number of maps actually timed."""
+    if rank != 0:
+        return
+    w = WORKLOADS[args.workload]
+    warm = max(1, min(args.warmup, 1))
+    for i in range(warm):
+        oracle_map_sample(w, i)
+    times = []
+    t_start = time.perf_counter()
+    for i in range(args.steps):
+        s, _ = oracle_map_sample(w, warm + i)
+        times.append(s)
+        if time.perf_counter() - t_start > args.ref_budget_s:
+            break
+    total = sum(times)
+    value = len(times) / total
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "maps/s", "n_gpus": world,
+            "steps": len(times), "warmup": warm, "ms_per_step": round(1e3 * total / len(times), 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "N": w.N, "npix": int(w.pixels().shape[0])},
+            "cpu_baseline": {"value": round(value, 6), "unit": "maps/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"{len(times)} full map(s) of {args.workload} by the numpy FP64 oracle "
+                                       f"(bounded to about {args.ref_budget_s:.0f} s)"},
+            "e2e": {"value": round(value, 6), "unit": "maps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--ref-budget-s", type=float, default=90.0)
+    ap.add_argument("--impl", default="cmb3d", choices=["cmb3d", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    run_cuda(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

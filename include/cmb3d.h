@@ -1,0 +1,229 @@
+/*
+ * cmb3d.h -- C ABI of the GB300 (sm_103a) library for simulating partial-sky
+ * CMB temperature maps with 3-D FFTs (the "3-D Fourier method" of Giner
+ * Mascarell & Bunn, "Simulating Partial Sky Cosmic Microwave Background Maps
+ * with 3D Fast Fourier Transforms").
+ *
+ * The method (paper Sec. II): given a 3-D power spectrum P_inf(k) whose
+ * correlation function matches the angular one of a target C_l (Sec. II.A-B),
+ * fill a periodic N^3 box of side L with complex normal Fourier coefficients of
+ * variance P_box(|k|) = P_inf(|k|) (2 pi / L)^3 (Eq. 2.11 for a cubic box),
+ * inverse-FFT it (Sec. II.D.1), and sample the field by interpolation at the
+ * pixel positions r * n_hat on a sphere of radius r centred in the box.
+ *
+ * Conventions used by every call:
+ *   - Every function returns CMB3D_OK (0) or a negative status and never throws
+ *     or aborts across the ABI.  Output buffers are undefined after an error.
+ *     cmb3d_strerror() names a status; cmb3d_error_detail() returns a message
+ *     about the most recent error on the calling thread.
+ *   - A plan is not thread-safe.  Work is enqueued on the CUDA stream passed
+ *     as `stream` (a cudaStream_t; NULL = legacy default stream); ordering and
+ *     synchronisation are the caller's, except where a call says it
+ *     synchronises.
+ *   - "device pointer" means memory of the plan's device (the device current
+ *     when cmb3d_plan was called); "host pointer" means ordinary host memory.
+ *     The plan copies every input array it is given; the caller keeps
+ *     ownership of all buffers it passes.
+ *   - Box layout: grid point (x, y, z) sits at (x, y, z) * L / N, periodic; the
+ *     sphere centre is the box centre, so pixel n_hat maps to grid coordinates
+ *     u = (r n_hat + L/2) / (L/N).  The real field is stored float[z][y][x].
+ *   - Randomness: realization `seed` is a pure function of (plan, spectrum,
+ *     seed); the Philox4x32-10 counter of Fourier mode (m_x, m_y, m_z) is
+ *     (m_x >> 1, m_y, m_z, 0) with key (seed low 32 bits, seed high 32 bits).
+ */
+#ifndef CMB3D_H
+#define CMB3D_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cmb3d_plan_s* cmb3d_plan_t;
+
+/* Status codes. */
+enum {
+  CMB3D_OK = 0,
+  CMB3D_EINVAL = -1,        /* bad argument (null pointer, size, range)            */
+  CMB3D_ENOMEM = -2,        /* host or device allocation failed                     */
+  CMB3D_ECUDA = -3,         /* a CUDA runtime call or kernel launch failed          */
+  CMB3D_ENOSPEC = -4,       /* realization requested before cmb3d_set_spectrum      */
+  CMB3D_ETIMEOUT = -5,      /* a bounded device-side wait gave up                   */
+  CMB3D_EUNSUPPORTED = -6   /* valid request outside what this build supports       */
+};
+
+/* Interpolation of the box field at the pixels (paper Sec. II.D.1). */
+enum {
+  CMB3D_TRILINEAR = 1,      /* 2x2x2 taps, weights (1-t, t)                          */
+  CMB3D_TRICUBIC = 3        /* 4x4x4 taps, Keys cubic convolution a = -1/2          */
+};
+
+/* Plan flags (bitwise OR). */
+enum {
+  CMB3D_FLAG_NONE = 0u,
+  CMB3D_FLAG_NO_SORT = 1u << 0,       /* gather in the caller's pixel order          */
+  CMB3D_FLAG_ALLOW_WRAP = 1u << 1,    /* permit L <= 2r (the sphere wraps around)    */
+  CMB3D_FLAG_STAGE_TIMING = 1u << 2   /* record CUDA events around every kernel      */
+};
+
+/* Spectrum kinds for cmb3d_set_spectrum. */
+enum {
+  CMB3D_SPEC_PK = 0,        /* x = k nodes, y = P_inf(k) at the nodes               */
+  CMB3D_SPEC_CL = 1         /* x = multipoles l, y = C_l (inverted to P_inf(k))     */
+};
+
+/* Kernel stages of one realization, for cmb3d_stage_times(). */
+enum {
+  CMB3D_STAGE_DRAW_ZFFT = 0,   /* Philox draw x sqrt(P_box), Hermitian, 1-D FFT along z */
+  CMB3D_STAGE_YFFT = 1,        /* 1-D FFT along y                                       */
+  CMB3D_STAGE_XC2R = 2,        /* 1-D complex-to-real FFT along x                       */
+  CMB3D_STAGE_GATHER = 3,      /* interpolation at the pixels                           */
+  CMB3D_NUM_STAGES = 4
+};
+
+/*
+ * Create a plan for an N^3 box of side L sampled at npix pixels on the sphere
+ * of radius r (paper Sec. II.C on the box, Sec. II.D.1 on sampling).
+ *
+ *   out      [out] receives the new plan (set to NULL on error).
+ *   N        points per axis; a power of two with 8 <= N <= 2048, else
+ *            CMB3D_EUNSUPPORTED.
+ *   L, r     box side and sphere radius, finite and > 0; L > 2r is required
+ *            unless flags has CMB3D_FLAG_ALLOW_WRAP (CMB3D_EINVAL).
+ *   pix_xyz  host pointer, npix x 3 doubles (x, y, z of each unit vector,
+ *            row-major); may be NULL when npix == 0.  Copied.
+ *   npix     number of pixels, 0 <= npix < 2^31.
+ *   interp   CMB3D_TRILINEAR or CMB3D_TRICUBIC.
+ *   flags    CMB3D_FLAG_* bits.
+ * Pixel positions are mapped once, in IEEE double precision evaluated as
+ * u = (r * n + 0.5 * L) / (L / N) with no fused multiply-add: the base cell
+ * floor(u) mod N is kept exactly and the fraction u - floor(u) is rounded to
+ * binary32.  Allocates the plan's device memory: 4 N^3 bytes for the box plus
+ * 20 bytes per pixel plus small tables.
+ */
+int cmb3d_plan(cmb3d_plan_t* out, int N, double L, double r,
+               const double* pix_xyz, int64_t npix, int interp, uint32_t flags);
+
+/*
+ * Set the box spectrum (paper Sec. II.A-C).
+ *
+ *   kind = CMB3D_SPEC_PK: x[0..n) are strictly increasing k >= 0 and y[0..n)
+ *     the values P_inf(k) >= 0 (host pointers, copied).  P_inf is linear in k
+ *     between nodes, equal to y[0] below x[0] and zero above x[n-1].
+ *     nkbins and fit_err are ignored (fit_err, if not NULL, is set to 0).
+ *   kind = CMB3D_SPEC_CL: x[0..n) are multipoles l >= 2 (integers, increasing)
+ *     and y[0..n) the target C_l > 0.  P_inf >= 0 is fitted on nkbins uniform
+ *     k nodes on [0, sqrt(3) pi N / L] by non-negative least squares on the
+ *     relation C_l = 16 pi^2 int k^2 P(k) j_l(k r)^2 dk (relative residuals);
+ *     nkbins must be in [8, 4096].  fit_err, if not NULL, receives the maximum
+ *     relative error of the forward-projected C_l.
+ * Then P_box(q) = P_inf(2 pi sqrt(q) / L) (2 pi / L)^3 (Eq. 2.11 with M = N)
+ * is tabulated for q = 0 .. 3 (N/2)^2 and the table sqrt(P_box / 2) is
+ * uploaded (one synchronous host-to-device copy).
+ * Errors: CMB3D_EINVAL for bad arrays, CMB3D_ECUDA for the upload.
+ */
+int cmb3d_set_spectrum(cmb3d_plan_t plan, int kind, const double* x, const double* y,
+                       int n, int nkbins, double* fit_err);
+
+/*
+ * Host-only form of the C_l inversion of cmb3d_set_spectrum(CMB3D_SPEC_CL),
+ * needing no GPU: fits P_inf >= 0 on nk uniform nodes of [0, sqrt(3) pi N / L]
+ * for a sphere of radius r.
+ *   ell, cl     host arrays of n multipoles (integers >= 2, increasing) and
+ *               C_l > 0.
+ *   knodes_out  host array of nk doubles receiving the k nodes.
+ *   pk_out      host array of nk doubles receiving P_inf at the nodes.
+ *   fit_err     may be NULL; receives the maximum relative C_l error.
+ * Errors: CMB3D_EINVAL for bad arguments; CMB3D_EUNSUPPORTED if the
+ * non-negative least-squares iteration does not converge.
+ */
+int cmb3d_fit_pk(const double* ell, const double* cl, int n, int N, double L, double r, int nk,
+                 double* knodes_out, double* pk_out, double* fit_err);
+
+/*
+ * Read back the plan's fitted P_inf(k) at n points (paper Sec. II.B output).
+ *   k   host pointer, n abscissae (input); pk host pointer, n values (output).
+ * Returns CMB3D_ENOSPEC before cmb3d_set_spectrum.
+ */
+int cmb3d_get_pk(cmb3d_plan_t plan, const double* k, double* pk, int n);
+
+/*
+ * One partial-sky map (paper Sec. II.D.1, the 3-D Fourier method): draw the
+ * Gaussian Fourier coefficients of realization `seed`, inverse-FFT the box and
+ * interpolate the field at the plan's pixels.
+ *   out_dev  device pointer to npix floats, written in the caller's pixel
+ *            order.  Caller-owned.
+ *   stream   cudaStream_t the kernels are enqueued on (asynchronous).
+ * Errors: CMB3D_ENOSPEC before cmb3d_set_spectrum; CMB3D_EINVAL for a NULL
+ * out_dev with npix > 0; CMB3D_ECUDA if a launch fails.
+ */
+int cmb3d_realize_sample(cmb3d_plan_t plan, uint64_t seed, float* out_dev, void* stream);
+
+/*
+ * The same map delivered to host memory: enqueues cmb3d_realize_sample into the
+ * plan's staging buffer, copies the npix floats to out_host (pinned memory is
+ * fastest) and synchronises the stream before returning.
+ */
+int cmb3d_realize_sample_to_host(cmb3d_plan_t plan, uint64_t seed, float* out_host,
+                                 void* stream);
+
+/*
+ * Many maps at once (batched form of Sec. II.D.1; the paper notes that one set
+ * of precomputed quantities serves many simulations, Sec. II.D.2, a remark that holds for the 3-D method too).
+ *   plans     host array of B plans that share N, L and interp (their pixel
+ *             sets and spectra may differ).
+ *   seeds     host array of B seeds; outs_dev host array of B device pointers,
+ *             each to that plan's npix floats.
+ * Errors: CMB3D_EINVAL if the plans differ in N, L or interp.
+ */
+int cmb3d_realize_sample_batch(const cmb3d_plan_t* plans, const uint64_t* seeds,
+                               float* const* outs_dev, int B, void* stream);
+
+/*
+ * Diagnostics of the intermediate stages of one realization (same seed
+ * convention as cmb3d_realize_sample):
+ *   cmb3d_draw_spectrum: the drawn half spectrum in the packed layout the
+ *     kernels use, float2 [m_z][m_y][m_x'] with m_x' = 0 .. N/2-1, where entry
+ *     m_x' = 0 holds T(0,m_y,m_z) + i T(N/2,m_y,m_z) and m_x' > 0 holds
+ *     T(m_x',m_y,m_z).  spec_dev: device pointer to N*N*N/2 float2.
+ *   cmb3d_realize_field: the real box field float[z][y][x] (N^3 floats).
+ */
+int cmb3d_draw_spectrum(cmb3d_plan_t plan, uint64_t seed, void* spec_dev, void* stream);
+int cmb3d_realize_field(cmb3d_plan_t plan, uint64_t seed, float* field_dev, void* stream);
+
+/*
+ * Philox4x32-10 words exactly as the draw kernel computes them: for i < n,
+ * out_dev[4i..4i+3] = Philox4x32-10(counter ctr_dev[4i..4i+3], key (seed lo,
+ * seed hi)).  Device pointers; n >= 0.
+ */
+int cmb3d_philox4x32_10(const uint32_t* ctr_dev, uint64_t seed, uint32_t* out_dev,
+                        int64_t n, void* stream);
+
+/*
+ * Per-stage device time in milliseconds accumulated since the last reset, for
+ * plans made with CMB3D_FLAG_STAGE_TIMING (CMB3D_EINVAL otherwise).  ms[0..n)
+ * receives stages CMB3D_STAGE_*; launches[0..n) (may be NULL) the number of
+ * kernel launches timed per stage.  Synchronises on the recorded events.
+ * reset != 0 clears the accumulators after reading.
+ */
+int cmb3d_stage_times(cmb3d_plan_t plan, double* ms, int64_t* launches, int n, int reset);
+
+/* Plan properties: N, number of pixels, and device bytes owned by the plan. */
+int cmb3d_plan_info(cmb3d_plan_t plan, int* N, int64_t* npix, int64_t* device_bytes);
+
+/* Release the plan and all device memory it owns (NULL is ignored). */
+void cmb3d_destroy(cmb3d_plan_t plan);
+
+/* Name of a status code (static string). */
+const char* cmb3d_strerror(int status);
+
+/* Message of the most recent error on the calling thread (static per thread). */
+const char* cmb3d_error_detail(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CMB3D_H */

@@ -1,0 +1,308 @@
+"""ctypes binding of the cmb3d C ABI (include/cmb3d.h).
+
+Argument marshalling only: every step of a realization runs in the CUDA
+kernels of libcmb3d.so.  Functions carry the C names; device buffers may be
+passed as torch CUDA tensors or raw integer addresses, host arrays as numpy
+arrays.  A missing library raises immediately: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcmb3d.so")
+
+CMB3D_OK = 0
+CMB3D_EINVAL = -1
+CMB3D_ENOMEM = -2
+CMB3D_ECUDA = -3
+CMB3D_ENOSPEC = -4
+CMB3D_ETIMEOUT = -5
+CMB3D_EUNSUPPORTED = -6
+
+CMB3D_TRILINEAR = 1
+CMB3D_TRICUBIC = 3
+
+CMB3D_FLAG_NONE = 0
+CMB3D_FLAG_NO_SORT = 1 << 0
+CMB3D_FLAG_ALLOW_WRAP = 1 << 1
+CMB3D_FLAG_STAGE_TIMING = 1 << 2
+
+CMB3D_SPEC_PK = 0
+CMB3D_SPEC_CL = 1
+
+CMB3D_STAGE_DRAW_ZFFT = 0
+CMB3D_STAGE_YFFT = 1
+CMB3D_STAGE_XC2R = 2
+CMB3D_STAGE_GATHER = 3
+CMB3D_NUM_STAGES = 4
+STAGE_NAMES = ("draw_zfft", "yfft", "xc2r", "gather")
+
+_vp = C.c_void_p
+_i32 = C.c_int
+_i64 = C.c_int64
+_u32 = C.c_uint32
+_u64 = C.c_uint64
+_dp = C.POINTER(C.c_double)
+
+# name -> (restype, argtypes); the full exported surface of include/cmb3d.h
+PROTOTYPES = {
+    "cmb3d_plan": (_i32, [C.POINTER(_vp), _i32, C.c_double, C.c_double, _dp, _i64, _i32, _u32]),
+    "cmb3d_set_spectrum": (_i32, [_vp, _i32, _dp, _dp, _i32, _i32, _dp]),
+    "cmb3d_fit_pk": (_i32, [_dp, _dp, _i32, _i32, C.c_double, C.c_double, _i32, _dp, _dp, _dp]),
+    "cmb3d_get_pk": (_i32, [_vp, _dp, _dp, _i32]),
+    "cmb3d_realize_sample": (_i32, [_vp, _u64, _vp, _vp]),
+    "cmb3d_realize_sample_to_host": (_i32, [_vp, _u64, _vp, _vp]),
+    "cmb3d_realize_sample_batch": (_i32, [C.POINTER(_vp), C.POINTER(_u64), C.POINTER(_vp), _i32, _vp]),
+    "cmb3d_draw_spectrum": (_i32, [_vp, _u64, _vp, _vp]),
+    "cmb3d_realize_field": (_i32, [_vp, _u64, _vp, _vp]),
+    "cmb3d_philox4x32_10": (_i32, [_vp, _u64, _vp, _i64, _vp]),
+    "cmb3d_stage_times": (_i32, [_vp, _dp, C.POINTER(_i64), _i32, _i32]),
+    "cmb3d_plan_info": (_i32, [_vp, C.POINTER(_i32), C.POINTER(_i64), C.POINTER(_i64)]),
+    "cmb3d_destroy": (None, [_vp]),
+    "cmb3d_strerror": (C.c_char_p, [_i32]),
+    "cmb3d_error_detail": (C.c_char_p, []),
+}
+
+_lib = None
+
+
+class Cmb3dError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        lib = load()
+        msg = lib.cmb3d_strerror(status).decode()
+        detail = lib.cmb3d_error_detail().decode()
+        super().__init__(f"{where}: {msg}" + (f" ({detail})" if detail else ""))
+
+
+def load(path: str | None = None):
+    """Load libcmb3d.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"cmb3d native library not found at {p}; build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = C.CDLL(p)
+    for name, (res, args) in PROTOTYPES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _check(status: int, where: str) -> None:
+    if status != CMB3D_OK:
+        raise Cmb3dError(status, where)
+
+
+def _dev_ptr(x) -> int | None:
+    """Device address of a torch CUDA tensor, or an integer address as given."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if hasattr(x, "is_cuda") and not x.is_cuda:
+            raise ValueError("expected a CUDA tensor")
+        return x.data_ptr()
+    raise TypeError(f"cannot take a device address of {type(x)!r}")
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        try:
+            import torch
+            return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+# --------------------------------------------------------------------------
+# C-named wrappers
+# --------------------------------------------------------------------------
+
+def cmb3d_plan(N: int, L: float, r: float, pix_xyz, interp: int = CMB3D_TRILINEAR,
+               flags: int = CMB3D_FLAG_NONE) -> int:
+    lib = load()
+    pix = _f64(pix_xyz).reshape(-1, 3)
+    h = _vp()
+    ptr = pix.ctypes.data_as(_dp) if pix.size else None
+    _check(lib.cmb3d_plan(C.byref(h), int(N), float(L), float(r), ptr, pix.shape[0], int(interp), int(flags)),
+           "cmb3d_plan")
+    return h.value
+
+
+def cmb3d_set_spectrum(plan: int, kind: int, x, y, nkbins: int = 256) -> float:
+    lib = load()
+    xa, ya = _f64(x), _f64(y)
+    if xa.shape != ya.shape or xa.ndim != 1:
+        raise ValueError("x and y must be 1-D arrays of equal length")
+    err = C.c_double(0.0)
+    _check(lib.cmb3d_set_spectrum(plan, int(kind), xa.ctypes.data_as(_dp), ya.ctypes.data_as(_dp), xa.size,
+                                  int(nkbins), C.byref(err)), "cmb3d_set_spectrum")
+    return err.value
+
+
+def cmb3d_fit_pk(ell, cl, N: int, L: float, r: float, nk: int = 256):
+    """Host-only C_l -> P_inf(k) inversion; returns (knodes, pk, max relative C_l error)."""
+    lib = load()
+    ea, ca = _f64(ell), _f64(cl)
+    if ea.shape != ca.shape or ea.ndim != 1:
+        raise ValueError("ell and cl must be 1-D arrays of equal length")
+    kn = np.empty(int(nk))
+    pk = np.empty(int(nk))
+    err = C.c_double(0.0)
+    _check(lib.cmb3d_fit_pk(ea.ctypes.data_as(_dp), ca.ctypes.data_as(_dp), ea.size, int(N), float(L), float(r),
+                            int(nk), kn.ctypes.data_as(_dp), pk.ctypes.data_as(_dp), C.byref(err)), "cmb3d_fit_pk")
+    return kn, pk, err.value
+
+
+def cmb3d_get_pk(plan: int, k) -> np.ndarray:
+    lib = load()
+    ka = _f64(k)
+    out = np.empty_like(ka)
+    _check(lib.cmb3d_get_pk(plan, ka.ctypes.data_as(_dp), out.ctypes.data_as(_dp), ka.size), "cmb3d_get_pk")
+    return out
+
+
+def cmb3d_realize_sample(plan: int, seed: int, out_dev, stream=None) -> None:
+    lib = load()
+    _check(lib.cmb3d_realize_sample(plan, int(seed) & 0xFFFFFFFFFFFFFFFF, _dev_ptr(out_dev), _stream_ptr(stream)),
+           "cmb3d_realize_sample")
+
+
+def cmb3d_realize_sample_to_host(plan: int, seed: int, out_host: np.ndarray, stream=None) -> None:
+    lib = load()
+    if out_host.dtype != np.float32 or not out_host.flags.c_contiguous:
+        raise ValueError("out_host must be a contiguous float32 array")
+    _check(lib.cmb3d_realize_sample_to_host(plan, int(seed) & 0xFFFFFFFFFFFFFFFF, out_host.ctypes.data,
+                                            _stream_ptr(stream)), "cmb3d_realize_sample_to_host")
+
+
+def cmb3d_realize_sample_batch(plans, seeds, outs_dev, stream=None) -> None:
+    lib = load()
+    B = len(plans)
+    if len(seeds) != B or len(outs_dev) != B:
+        raise ValueError("plans, seeds and outs_dev must have equal lengths")
+    hp = (_vp * B)(*plans)
+    hs = (_u64 * B)(*[int(s) & 0xFFFFFFFFFFFFFFFF for s in seeds])
+    ho = (_vp * B)(*[_dev_ptr(o) for o in outs_dev])
+    _check(lib.cmb3d_realize_sample_batch(hp, hs, ho, B, _stream_ptr(stream)), "cmb3d_realize_sample_batch")
+
+
+def cmb3d_draw_spectrum(plan: int, seed: int, spec_dev, stream=None) -> None:
+    lib = load()
+    _check(lib.cmb3d_draw_spectrum(plan, int(seed) & 0xFFFFFFFFFFFFFFFF, _dev_ptr(spec_dev), _stream_ptr(stream)),
+           "cmb3d_draw_spectrum")
+
+
+def cmb3d_realize_field(plan: int, seed: int, field_dev, stream=None) -> None:
+    lib = load()
+    _check(lib.cmb3d_realize_field(plan, int(seed) & 0xFFFFFFFFFFFFFFFF, _dev_ptr(field_dev), _stream_ptr(stream)),
+           "cmb3d_realize_field")
+
+
+def cmb3d_philox4x32_10(ctr_dev, seed: int, out_dev, n: int, stream=None) -> None:
+    lib = load()
+    _check(lib.cmb3d_philox4x32_10(_dev_ptr(ctr_dev), int(seed) & 0xFFFFFFFFFFFFFFFF, _dev_ptr(out_dev), int(n),
+                                   _stream_ptr(stream)), "cmb3d_philox4x32_10")
+
+
+def cmb3d_stage_times(plan: int, reset: bool = True) -> tuple[np.ndarray, np.ndarray]:
+    lib = load()
+    ms = np.zeros(CMB3D_NUM_STAGES)
+    cnt = np.zeros(CMB3D_NUM_STAGES, dtype=np.int64)
+    _check(lib.cmb3d_stage_times(plan, ms.ctypes.data_as(_dp), cnt.ctypes.data_as(C.POINTER(_i64)),
+                                 CMB3D_NUM_STAGES, int(bool(reset))), "cmb3d_stage_times")
+    return ms, cnt
+
+
+def cmb3d_plan_info(plan: int) -> tuple[int, int, int]:
+    lib = load()
+    n, npix, nbytes = _i32(), _i64(), _i64()
+    _check(lib.cmb3d_plan_info(plan, C.byref(n), C.byref(npix), C.byref(nbytes)), "cmb3d_plan_info")
+    return n.value, npix.value, nbytes.value
+
+
+def cmb3d_destroy(plan: int) -> None:
+    load().cmb3d_destroy(plan)
+
+
+def cmb3d_strerror(status: int) -> str:
+    return load().cmb3d_strerror(int(status)).decode()
+
+
+def cmb3d_error_detail() -> str:
+    return load().cmb3d_error_detail().decode()
+
+
+# --------------------------------------------------------------------------
+# Convenience object
+# --------------------------------------------------------------------------
+
+class Plan:
+    """Owns a cmb3d plan handle; methods forward to the C functions."""
+
+    def __init__(self, N, L, r, pix_xyz, interp=CMB3D_TRILINEAR, flags=CMB3D_FLAG_NONE):
+        self.handle = cmb3d_plan(N, L, r, pix_xyz, interp, flags)
+        self.N = int(N)
+        self.npix = int(np.asarray(pix_xyz).reshape(-1, 3).shape[0])
+
+    def set_pk(self, k, pk) -> None:
+        cmb3d_set_spectrum(self.handle, CMB3D_SPEC_PK, k, pk)
+
+    def set_cl(self, ell, cl, nkbins: int = 256) -> float:
+        return cmb3d_set_spectrum(self.handle, CMB3D_SPEC_CL, ell, cl, nkbins)
+
+    def realize_sample(self, seed, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.npix, dtype=torch.float32, device="cuda")
+        cmb3d_realize_sample(self.handle, seed, out, stream)
+        return out
+
+    def realize_field(self, seed, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty((self.N, self.N, self.N), dtype=torch.float32, device="cuda")
+        cmb3d_realize_field(self.handle, seed, out, stream)
+        return out
+
+    def draw_spectrum(self, seed, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty((self.N, self.N, self.N // 2, 2), dtype=torch.float32, device="cuda")
+        cmb3d_draw_spectrum(self.handle, seed, out, stream)
+        return out
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            cmb3d_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

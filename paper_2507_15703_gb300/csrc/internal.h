@@ -1,0 +1,45 @@
+// Internal interface between the host library (plan.cpp) and the CUDA kernel
+// launchers (*.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace cmb3d {
+
+// Packed half-spectrum buffer: float2 [N][N][N/2]; entry m_x' = 0 holds
+// T(0,.,.) + i T(N/2,.,.).  After the three passes it holds float [N][N][N].
+
+// Draw the Gaussian Fourier coefficients of realization key and inverse-FFT
+// every (m_y, m_x') column along z.  amp[q] = sqrt(P_box(q) / 2) for
+// q = m_x^2 + m_y^2 + m_z^2; tw[m] = exp(+2 pi i m / N), m < N.
+cudaError_t launch_draw_zfft(int N, float2* buf, const float* amp, const float2* tw,
+                             uint64_t seed, cudaStream_t s);
+
+// Diagnostic: the drawn packed half spectrum [m_z][m_y][m_x'], untransformed.
+cudaError_t launch_draw_only(int N, float2* buf, const float* amp, uint64_t seed, cudaStream_t s);
+
+// Inverse FFT of every (z, m_x') column along y, in place.
+cudaError_t launch_yfft(int N, float2* buf, const float2* tw, cudaStream_t s);
+
+// Complex-to-real inverse FFT of every (z, y) row along x, in place.
+cudaError_t launch_xc2r(int N, float2* buf, const float2* tw, cudaStream_t s);
+
+// Interpolate the field float[z][y][x] at npix pixels.  tab[i] = (tx, ty, tz,
+// packed base cell) in gather order; out[perm[i]] receives pixel i (perm may
+// be NULL for the identity).
+cudaError_t launch_gather(int N, int interp, const float* field, const float4* tab,
+                          const int32_t* perm, float* out, int64_t npix, cudaStream_t s);
+
+// Philox4x32-10 words of n counters (uint4 each).
+cudaError_t launch_philox(const uint32_t* ctr, uint64_t seed, uint32_t* out, int64_t n,
+                          cudaStream_t s);
+
+// Packing of a pixel's base cell (bx, by, bz), each < 2048, into the fourth
+// word of its table entry: bx | by << 11 | (bz & 1023) << 22, with bit 10 of bz
+// carried in the sign bit of tz (tz >= 0).
+inline uint32_t pack_cell(uint32_t bx, uint32_t by, uint32_t bz) {
+  return bx | (by << 11) | ((bz & 1023u) << 22);
+}
+
+}  // namespace cmb3d

@@ -7,7 +7,7 @@ quantity the path needs:
         = 16 pi^2 A pi / (4 r s^2) exp(-r^2/(2 s^2)) I_{l+1/2}(r^2 / (2 s^2))
     (Weber's second exponential integral with j_l = sqrt(pi/2x) J_{l+1/2});
   * Eq. (2.1) with those C_l must equal xi_inf at the chord of Eq. (2.3).
-Eq. (2.12) for the cubic box is pinned on a spectrum that is linear in k.
+Eq. (2.11) for the cubic box is pinned on a spectrum that is linear in k.
 """
 import math
 
