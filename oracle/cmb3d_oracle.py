@@ -8,7 +8,7 @@ anything under ``oracle/``, and this module imports nothing from the product.
 What is computed (paper: Giner Mascarell & Bunn, "Simulating Partial Sky CMB
 Maps with 3D Fast Fourier Transforms"):
 
-* Sec. II.C, Eq. (2.9)-(2.12): the box power per Fourier mode,
+* Sec. II.C, Eq. (2.8)-(2.11): the box power per Fourier mode,
   P_box = P_inf(k) (2 pi / dp)^3 / (M N^2); for the cubic N^3 box of side L
   this is P_inf(k) (2 pi / L)^3.
 * Sec. II.D.1: every mode of the box gets a complex normal number of mean 0 and
@@ -160,7 +160,7 @@ def p_inf_at(k, knodes, pnodes) -> np.ndarray:
 
 
 def p_box_of_q(N: int, L: float, knodes, pnodes) -> np.ndarray:
-    """P_box(q) for q = 0 .. 3 (N/2)^2, Eq. (2.12) for the cubic box:
+    """P_box(q) for q = 0 .. 3 (N/2)^2, Eq. (2.11) for the cubic box:
     P_box = P_inf(k_f sqrt(q)) k_f^3 with k_f = 2 pi / L = 2 pi / (N dp)."""
     kf = 2.0 * np.pi / L
     q = np.arange(3 * (N // 2) ** 2 + 1, dtype=np.float64)
