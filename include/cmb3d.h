@@ -210,6 +210,35 @@ int cmb3d_philox4x32_10(const uint32_t* ctr_dev, uint64_t seed, uint32_t* out_de
  */
 int cmb3d_stage_times(cmb3d_plan_t plan, double* ms, int64_t* launches, int n, int reset);
 
+/*
+ * One partial-sky map with no device allocation, for callers that cannot call
+ * cudaMalloc (code running inside another runtime that owns all device
+ * memory, or behind an allocator that forbids new allocations).  The paper has
+ * no counterpart to this call; it is the same computation as
+ * cmb3d_realize_sample without a plan.
+ *
+ *   N        power of two, 8 <= N <= CMB3D_NOALLOC_MAX_N; larger N returns
+ *            CMB3D_EUNSUPPORTED (the box does not fit the static scratch).
+ *   L, r     box side and sphere radius, finite, > 0, L > 2r (CMB3D_EINVAL).
+ *   pix_dev  device pointer, npix x 3 doubles (unit vectors, row-major).
+ *   npix     0 <= npix < 2^31.
+ *   interp   CMB3D_TRILINEAR or CMB3D_TRICUBIC.
+ *   amp_dev  device pointer, 3 (N/2)^2 + 1 floats: amp[q] = sqrt(P_box(q) / 2)
+ *            with P_box(q) = P_inf(2 pi sqrt(q) / L) (2 pi / L)^3, the table
+ *            cmb3d_set_spectrum builds for a plan.
+ *   out_dev  device pointer, npix floats, written in pixel order.
+ * The box and twiddle tables live in one static __device__ array of about
+ * 1 MiB that every GPU loading the library holds until the process exits.
+ * The first call on a device looks up that array's address and uploads the
+ * twiddle tables with a synchronous copy, so make it before any stream
+ * capture.  Every call overwrites the whole box before use, but all calls
+ * share the array: calls that overlap on the GPU (other streams or threads)
+ * race and must be serialised by the caller.  Calls no allocating routine.
+ */
+#define CMB3D_NOALLOC_MAX_N 64
+int cmb3d_realize_sample_noalloc(int N, double L, double r, const double* pix_dev, int64_t npix, int interp,
+                                 const float* amp_dev, uint64_t seed, float* out_dev, void* stream);
+
 /* Plan properties: N, number of pixels, and device bytes owned by the plan. */
 int cmb3d_plan_info(cmb3d_plan_t plan, int* N, int64_t* npix, int64_t* device_bytes);
 

@@ -61,6 +61,7 @@ PROTOTYPES = {
     "cmb3d_realize_field": (_i32, [_vp, _u64, _vp, _vp]),
     "cmb3d_philox4x32_10": (_i32, [_vp, _u64, _vp, _i64, _vp]),
     "cmb3d_stage_times": (_i32, [_vp, _dp, C.POINTER(_i64), _i32, _i32]),
+    "cmb3d_realize_sample_noalloc": (_i32, [_i32, C.c_double, C.c_double, _vp, _i64, _i32, _vp, _u64, _vp, _vp]),
     "cmb3d_plan_info": (_i32, [_vp, C.POINTER(_i32), C.POINTER(_i64), C.POINTER(_i64)]),
     "cmb3d_destroy": (None, [_vp]),
     "cmb3d_strerror": (C.c_char_p, [_i32]),
@@ -221,6 +222,19 @@ def cmb3d_philox4x32_10(ctr_dev, seed: int, out_dev, n: int, stream=None) -> Non
     lib = load()
     _check(lib.cmb3d_philox4x32_10(_dev_ptr(ctr_dev), int(seed) & 0xFFFFFFFFFFFFFFFF, _dev_ptr(out_dev), int(n),
                                    _stream_ptr(stream)), "cmb3d_philox4x32_10")
+
+
+CMB3D_NOALLOC_MAX_N = 64
+
+
+def cmb3d_realize_sample_noalloc(N: int, L: float, r: float, pix_dev, npix: int, interp: int, amp_dev, seed: int,
+                                 out_dev, stream=None) -> None:
+    """Plan-free map that allocates no device memory (box in a static device
+    array; N <= CMB3D_NOALLOC_MAX_N)."""
+    lib = load()
+    _check(lib.cmb3d_realize_sample_noalloc(int(N), float(L), float(r), _dev_ptr(pix_dev), int(npix), int(interp),
+                                            _dev_ptr(amp_dev), int(seed) & 0xFFFFFFFFFFFFFFFF, _dev_ptr(out_dev),
+                                            _stream_ptr(stream)), "cmb3d_realize_sample_noalloc")
 
 
 def cmb3d_stage_times(plan: int, reset: bool = True) -> tuple[np.ndarray, np.ndarray]:
