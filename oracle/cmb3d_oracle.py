@@ -43,8 +43,8 @@ reason in the design notes of the repository):
    kernel (a = -1/2), with periodic wrap.
 8. Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) keyed by
    the 64-bit seed (low word, high word).  Mode (m_x, m_y, m_z) (array indices)
-   uses counter (m_x >> 1, m_y, m_z, 0); even m_x takes output words (0, 1),
-   odd m_x words (2, 3).  A word w becomes the uniform ((w >> 9) + 1/2) 2^-23,
+   uses counter (m_x, m_y, m_z mod N/2, 0); m_z < N/2 takes output words (0, 1),
+   m_z >= N/2 words (2, 3).  A word w becomes the uniform ((w >> 9) + 1/2) 2^-23,
    which is exact in binary32 as well as binary64, and two uniforms become
    two normals by the Box-Muller transform.  On the Hermitian planes
    m_x in {0, N/2} the mode with the smaller index m_z N + m_y of a conjugate
@@ -116,20 +116,22 @@ def box_muller(u0, u1):
 
 def unit_normals_half(N: int, seed: int) -> np.ndarray:
     """g1 + i g2 drawn from each mode's own counter, for every mode of the half
-    spectrum, shape (N, N, N/2+1) indexed [m_z, m_y, m_x] (no symmetry yet)."""
+    spectrum, shape (N, N, N/2+1) indexed [m_z, m_y, m_x] (no symmetry yet).
+    Counter (m_x, m_y, m_z mod N/2, 0) serves the two modes m_z < N/2 (words
+    0, 1) and m_z + N/2 (words 2, 3)."""
     k0, k1 = seed_key(seed)
-    nq = N // 4 + 1                         # counters m_x >> 1 = 0 .. N/4
-    mz, my, mx2 = np.meshgrid(np.arange(N, dtype=np.uint64), np.arange(N, dtype=np.uint64),
-                              np.arange(nq, dtype=np.uint64), indexing="ij")
-    w0, w1, w2, w3 = philox4x32_10(mx2, my, mz, 0, k0, k1)
-    del mz, my, mx2
-    ge1, ge2 = box_muller(uniform_from_word(w0), uniform_from_word(w1))   # even m_x
-    go1, go2 = box_muller(uniform_from_word(w2), uniform_from_word(w3))   # odd m_x
+    h = N // 2
+    mz, my, mx = np.meshgrid(np.arange(h, dtype=np.uint64), np.arange(N, dtype=np.uint64),
+                             np.arange(h + 1, dtype=np.uint64), indexing="ij")
+    w0, w1, w2, w3 = philox4x32_10(mx, my, mz, 0, k0, k1)
+    del mz, my, mx
+    lo1, lo2 = box_muller(uniform_from_word(w0), uniform_from_word(w1))   # m_z < N/2
+    hi1, hi2 = box_muller(uniform_from_word(w2), uniform_from_word(w3))   # m_z >= N/2
     del w0, w1, w2, w3
-    g = np.empty((N, N, 2 * nq), dtype=np.complex128)
-    g[:, :, 0::2] = ge1 + 1j * ge2
-    g[:, :, 1::2] = go1 + 1j * go2
-    return g[:, :, : N // 2 + 1]
+    g = np.empty((N, N, h + 1), dtype=np.complex128)
+    g[:h] = lo1 + 1j * lo2
+    g[h:] = hi1 + 1j * hi2
+    return g
 
 
 # --------------------------------------------------------------------------

@@ -69,7 +69,7 @@ def test_philox_matches_independent_implementation():
         ctr = rng.integers(0, 2 ** 32, size=(37, 4), dtype=np.uint64)
         ctr[0] = 0
         ctr[1] = 0xFFFFFFFF
-        ctr[2] = [5, 17, 300, 0]            # a typical mode counter (m_x>>1, m_y, m_z, 0)
+        ctr[2] = [5, 17, 300, 0]            # a typical mode counter (m_x, m_y, m_z mod N/2, 0)
         # the triton seed argument is a signed 64-bit integer with the same bits
         sarg = s - (1 << 64) if s >= (1 << 63) else s
         reqs.append((sarg, ctr.tolist()))
