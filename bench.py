@@ -135,6 +135,7 @@ KERNEL_SOURCES = {
     "yfft": ["paper_2507_15703_gb300/csrc/fft_passes.cu", "paper_2507_15703_gb300/csrc/device_common.cuh"],
     "xc2r": ["paper_2507_15703_gb300/csrc/fft_passes.cu", "paper_2507_15703_gb300/csrc/device_common.cuh"],
     "gather": ["paper_2507_15703_gb300/csrc/gather.cu"],
+    "yx_fused": ["paper_2507_15703_gb300/csrc/fft_passes.cu", "paper_2507_15703_gb300/csrc/device_common.cuh"],
 }
 
 
@@ -159,7 +160,7 @@ def algorithmic_bytes(N: int, npix: int) -> dict:
     pixel and writes 4 B per pixel (field reads are cache-dependent and not
     counted)."""
     box = 4 * N ** 3
-    return {"draw_zfft": box, "yfft": 2 * box, "xc2r": 2 * box, "gather": 24 * npix}
+    return {"draw_zfft": box, "yfft": 2 * box, "xc2r": 2 * box, "gather": 24 * npix, "yx_fused": 2 * box}
 
 
 # --------------------------------------------------------------------------
@@ -178,7 +179,12 @@ def run_cuda(args, rank, world, local):
     ell, cl = w.cl()
 
     t0 = time.time()
-    plan = cmb3d.Plan(w.N, w.L, w.r, pix, w.interp, cmb3d.CMB3D_FLAG_STAGE_TIMING)
+    flags = cmb3d.CMB3D_FLAG_STAGE_TIMING | cmb3d.CMB3D_FLAG_AUTOTUNE
+    if args.three_pass:
+        flags |= cmb3d.CMB3D_FLAG_THREE_PASS
+    if args.fused:
+        flags |= cmb3d.CMB3D_FLAG_FUSED_YX
+    plan = cmb3d.Plan(w.N, w.L, w.r, pix, w.interp, flags)
     fit_err = plan.set_cl(ell, cl, w.nkbins)
     setup_s = time.time() - t0
     stream = torch.cuda.current_stream(dev)
@@ -199,6 +205,10 @@ def run_cuda(args, rank, world, local):
         plan.realize_sample(seed0 + i, out, stream)
     torch.cuda.synchronize(dev)
     cmb3d.cmb3d_stage_times(plan.handle, reset=True)
+    schedule = cmb3d.cmb3d_plan_schedule(plan.handle)
+    if args.sweep and rank == 0:
+        sweep(plan, out, stream, w.N, seed0)
+        cmb3d.cmb3d_plan_set_schedule(plan.handle, schedule)
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -249,6 +259,8 @@ def run_cuda(args, rank, world, local):
     kernels = {}
     for i, name in enumerate(names):
         n = int(stage_n[i])
+        if n == 0:
+            continue
         avg_ms = stage_ms[i] / max(n, 1)
         gbs = ab[name] / (avg_ms / 1e3) / 1e9 if n else None
         kernels[name] = {"launches": n, "avg_ms": round(avg_ms, 5), "share": round(stage_ms[i] / max(stage_ms.sum(), 1e-12), 4),
@@ -273,6 +285,8 @@ def run_cuda(args, rank, world, local):
         "config": {"workload": args.workload, "N": w.N, "L_over_r": w.L_over_r, "npix": npix, "fsky": w.fsky,
                    "interp": "tricubic" if w.interp == 3 else "trilinear", "lmax": w.lmax, "nkbins": w.nkbins,
                    "parallelism": f"replicas x{world}",
+                   "schedule": {"draw": schedule[0], "y": schedule[1], "x": schedule[2], "fused_yx": schedule[3],
+                                "restriction": "three-pass" if args.three_pass else "fused" if args.fused else "autotuned"},
                    "l2": f"no flush: per-map working set {per_map_bytes / 2**30:.2f} GiB > 129 MiB L2",
                    "cl_fit_max_rel_err": fit_err, "plan_setup_s": round(setup_s, 2)},
         "achieved_gbs_alg_per_map": round(per_map_bytes * value / world / 1e9, 1),
@@ -290,6 +304,29 @@ def run_cuda(args, rank, world, local):
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def sweep(plan, out, stream, N, seed0, reps=20):
+    """Time every kernel variant (stage events) and print one JSON line per
+    schedule to stderr."""
+    import torch
+    from paper_2507_15703_gb300 import cmb3d
+    scheds = [(d, 0, 0, -1) for d in range(3)] + [(0, y, 0, -1) for y in range(3)] + \
+             [(0, 0, x, -1) for x in range(3)] + [(0, -1, -1, f) for f in range(2)]
+    for sc in scheds:
+        try:
+            cmb3d.cmb3d_plan_set_schedule(plan.handle, sc)
+        except cmb3d.Cmb3dError:
+            continue
+        for i in range(3):
+            plan.realize_sample(seed0 + i, out, stream)
+        torch.cuda.synchronize()
+        cmb3d.cmb3d_stage_times(plan.handle, reset=True)
+        for i in range(reps):
+            plan.realize_sample(seed0 + i, out, stream)
+        ms, n = cmb3d.cmb3d_stage_times(plan.handle, reset=True)
+        per = {name: round(float(ms[k] / n[k]), 5) for k, name in enumerate(cmb3d.STAGE_NAMES) if n[k]}
+        print(json.dumps({"sweep": list(sc), "avg_ms": per}), file=sys.stderr, flush=True)
 
 
 # --------------------------------------------------------------------------
@@ -358,6 +395,9 @@ def main():
     ap.add_argument("--impl", default="cmb3d", choices=["cmb3d", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--three-pass", action="store_true", help="only separate y and x passes")
+    ap.add_argument("--fused", action="store_true", help="only the fused y+x pass")
+    ap.add_argument("--sweep", action="store_true", help="also time every kernel variant (stderr)")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":

@@ -28,8 +28,9 @@
  *     sphere centre is the box centre, so pixel n_hat maps to grid coordinates
  *     u = (r n_hat + L/2) / (L/N).  The real field is stored float[z][y][x].
  *   - Randomness: realization `seed` is a pure function of (plan, spectrum,
- *     seed); the Philox4x32-10 counter of Fourier mode (m_x, m_y, m_z) is
- *     (m_x >> 1, m_y, m_z, 0) with key (seed low 32 bits, seed high 32 bits).
+ *     seed); Fourier mode (m_x, m_y, m_z) draws from the Philox4x32-10 counter
+ *     (m_x, m_y, m_z mod N/2, 0) with key (seed low 32 bits, seed high 32
+ *     bits), words (0,1) for m_z < N/2 and (2,3) otherwise.
  */
 #ifndef CMB3D_H
 #define CMB3D_H
@@ -65,7 +66,13 @@ enum {
   CMB3D_FLAG_NONE = 0u,
   CMB3D_FLAG_NO_SORT = 1u << 0,       /* gather in the caller's pixel order          */
   CMB3D_FLAG_ALLOW_WRAP = 1u << 1,    /* permit L <= 2r (the sphere wraps around)    */
-  CMB3D_FLAG_STAGE_TIMING = 1u << 2   /* record CUDA events around every kernel      */
+  CMB3D_FLAG_STAGE_TIMING = 1u << 2,  /* record CUDA events around every kernel      */
+  CMB3D_FLAG_THREE_PASS = 1u << 3,    /* only separate y and x passes                  */
+  CMB3D_FLAG_FUSED_YX = 1u << 4,      /* the fused y+x pass where it exists
+                                         (128 <= N <= 1024)                            */
+  CMB3D_FLAG_AUTOTUNE = 1u << 5       /* at the first realization, time every kernel
+                                         shape of this N and keep the fastest (cached
+                                         per device and N for the process)            */
 };
 
 /* Spectrum kinds for cmb3d_set_spectrum. */
@@ -80,7 +87,8 @@ enum {
   CMB3D_STAGE_YFFT = 1,        /* 1-D FFT along y                                       */
   CMB3D_STAGE_XC2R = 2,        /* 1-D complex-to-real FFT along x                       */
   CMB3D_STAGE_GATHER = 3,      /* interpolation at the pixels                           */
-  CMB3D_NUM_STAGES = 4
+  CMB3D_STAGE_YX_FUSED = 4,    /* y and x passes fused per z-plane (cluster, via L2)    */
+  CMB3D_NUM_STAGES = 5
 };
 
 /*
@@ -238,6 +246,23 @@ int cmb3d_stage_times(cmb3d_plan_t plan, double* ms, int64_t* launches, int n, i
 #define CMB3D_NOALLOC_MAX_N 64
 int cmb3d_realize_sample_noalloc(int N, double L, double r, const double* pix_dev, int64_t npix, int interp,
                                  const float* amp_dev, uint64_t seed, float* out_dev, void* stream);
+
+/*
+ * The kernel shapes the plan uses: sched[0] = draw+z variant, sched[1] = y
+ * variant, sched[2] = x variant (both -1 when fused), sched[3] = fused y+x
+ * variant (-1 when separate).  Variant 0 is each kernel's default shape; with
+ * CMB3D_FLAG_AUTOTUNE the values are final after the first realization.
+ * sched: host array of 4 ints.
+ */
+int cmb3d_plan_schedule(cmb3d_plan_t plan, int* sched);
+
+/*
+ * Pin the kernel shapes (same layout as cmb3d_plan_schedule; sched[3] >= 0
+ * selects the fused y+x pass and then sched[1], sched[2] are ignored).  Turns
+ * off a pending autotune.  CMB3D_EINVAL for a variant out of range or one the
+ * plan's flags exclude.  sched: host array of 4 ints.
+ */
+int cmb3d_plan_set_schedule(cmb3d_plan_t plan, const int* sched);
 
 /* Plan properties: N, number of pixels, and device bytes owned by the plan. */
 int cmb3d_plan_info(cmb3d_plan_t plan, int* N, int64_t* npix, int64_t* device_bytes);

@@ -30,6 +30,9 @@ CMB3D_FLAG_NONE = 0
 CMB3D_FLAG_NO_SORT = 1 << 0
 CMB3D_FLAG_ALLOW_WRAP = 1 << 1
 CMB3D_FLAG_STAGE_TIMING = 1 << 2
+CMB3D_FLAG_THREE_PASS = 1 << 3
+CMB3D_FLAG_FUSED_YX = 1 << 4
+CMB3D_FLAG_AUTOTUNE = 1 << 5
 
 CMB3D_SPEC_PK = 0
 CMB3D_SPEC_CL = 1
@@ -38,8 +41,9 @@ CMB3D_STAGE_DRAW_ZFFT = 0
 CMB3D_STAGE_YFFT = 1
 CMB3D_STAGE_XC2R = 2
 CMB3D_STAGE_GATHER = 3
-CMB3D_NUM_STAGES = 4
-STAGE_NAMES = ("draw_zfft", "yfft", "xc2r", "gather")
+CMB3D_STAGE_YX_FUSED = 4
+CMB3D_NUM_STAGES = 5
+STAGE_NAMES = ("draw_zfft", "yfft", "xc2r", "gather", "yx_fused")
 
 _vp = C.c_void_p
 _i32 = C.c_int
@@ -63,6 +67,8 @@ PROTOTYPES = {
     "cmb3d_stage_times": (_i32, [_vp, _dp, C.POINTER(_i64), _i32, _i32]),
     "cmb3d_realize_sample_noalloc": (_i32, [_i32, C.c_double, C.c_double, _vp, _i64, _i32, _vp, _u64, _vp, _vp]),
     "cmb3d_plan_info": (_i32, [_vp, C.POINTER(_i32), C.POINTER(_i64), C.POINTER(_i64)]),
+    "cmb3d_plan_schedule": (_i32, [_vp, C.POINTER(_i32)]),
+    "cmb3d_plan_set_schedule": (_i32, [_vp, C.POINTER(_i32)]),
     "cmb3d_destroy": (None, [_vp]),
     "cmb3d_strerror": (C.c_char_p, [_i32]),
     "cmb3d_error_detail": (C.c_char_p, []),
@@ -251,6 +257,20 @@ def cmb3d_plan_info(plan: int) -> tuple[int, int, int]:
     n, npix, nbytes = _i32(), _i64(), _i64()
     _check(lib.cmb3d_plan_info(plan, C.byref(n), C.byref(npix), C.byref(nbytes)), "cmb3d_plan_info")
     return n.value, npix.value, nbytes.value
+
+
+def cmb3d_plan_schedule(plan: int) -> tuple[int, int, int, int]:
+    """(draw variant, y variant, x variant, fused variant); -1 marks unused."""
+    lib = load()
+    out = (_i32 * 4)()
+    _check(lib.cmb3d_plan_schedule(plan, out), "cmb3d_plan_schedule")
+    return tuple(out)
+
+
+def cmb3d_plan_set_schedule(plan: int, sched) -> None:
+    lib = load()
+    arr = (_i32 * 4)(*[int(v) for v in sched])
+    _check(lib.cmb3d_plan_set_schedule(plan, arr), "cmb3d_plan_set_schedule")
 
 
 def cmb3d_destroy(plan: int) -> None:

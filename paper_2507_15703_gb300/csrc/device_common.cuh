@@ -121,12 +121,17 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
   return c;
 }
 
-// Uniform in (0,1): ((w >> 9) + 1/2) 2^-23, exact in binary32.
+// Uniform in (0,1): ((w >> 9) + 1/2) 2^-23, exact in binary32.  The top 23
+// bits become the mantissa of 1 + (w >> 9) 2^-23; subtracting 1 and adding
+// 2^-24 are both exact, so no integer-to-float conversion is needed.
 __device__ __forceinline__ float uniform_from_word(uint32_t w) {
-  return (static_cast<float>(w >> 9) + 0.5f) * 1.1920928955078125e-07f;
+  return (__uint_as_float(0x3F800000u | (w >> 9)) - 1.0f) + 5.9604644775390625e-08f;
 }
 
-// Box-Muller: two standard normals (g1, g2) from two uniforms.
+// Box-Muller: two standard normals (g1, g2) = sqrt(-2 ln u0) (cos 2 pi u1,
+// sin 2 pi u1), with the accurate logarithm and sincospi: the hardware
+// sine/cosine (about 2^-21 absolute) put the field's worst point above the
+// 1e-5 FP32-path tolerance.
 __device__ __forceinline__ float2 box_muller(uint32_t w0, uint32_t w1) {
   const float u0 = uniform_from_word(w0), u1 = uniform_from_word(w1);
   const float rad = sqrtf(-2.0f * logf(u0));

@@ -18,45 +18,70 @@
 namespace cmb3d {
 namespace {
 
-// Fourier coefficient of mode (mx, my, mz) on a Hermitian plane mx in {0, N/2}:
-// the mode with the smaller index mz N + my of a conjugate pair draws from its
-// own counter and its partner takes the conjugate; self-conjugate modes are
-// real with variance P_box; the DC mode is zero.
+// Fourier coefficients of the modes (mx, my, mz) and (mx, my, mz + N/2),
+// mz < N/2, which share the Philox counter (mx, my, mz, 0): words (0, 1) draw
+// the first, words (2, 3) the second.
+
+// On a Hermitian plane mx in {0, N/2}: the mode with the smaller index
+// mz N + my of a conjugate pair draws from its own counter and its partner
+// takes the conjugate; self-conjugate modes are real with variance P_box; the
+// DC mode is zero.  The partners of the two modes also share one counter.
 template <int N>
-__device__ __forceinline__ float2 draw_hermitian(int mx, int my, int mz, const float* __restrict__ amp,
-                                                 uint2 key) {
-  const int py = (N - my) & (N - 1), pz = (N - mz) & (N - 1);
-  const int lin = mz * N + my, plin = pz * N + py;
-  const int fy = my <= N / 2 ? my : my - N, fz = mz <= N / 2 ? mz : mz - N;
-  const int q = mx * mx + fy * fy + fz * fz;
-  const float a = __ldg(amp + q);
-  if (lin == plin) {
-    if (q == 0) return make_float2(0.f, 0.f);
-    const uint4 w = philox4x32_10(make_uint4(mx >> 1, my, mz, 0u), key);
-    const float2 g = box_muller(w.x, w.y);
-    return make_float2(a * 1.41421356237309505f * g.x, 0.f);
+__device__ __forceinline__ void draw_hermitian_pair(int mx, int my, int mz, const float* __restrict__ amp,
+                                                    uint2 key, float2& lo, float2& hi) {
+  constexpr int H = N / 2;
+  const int py = (N - my) & (N - 1);
+  const int pz_lo = (N - mz) & (N - 1), pz_hi = (pz_lo + H) & (N - 1);
+  const int fy = my <= H ? my : my - N;
+  const int q_lo = mx * mx + fy * fy + mz * mz;
+  const int fz_hi = mz + H <= H ? mz + H : mz + H - N;
+  const int q_hi = mx * mx + fy * fy + fz_hi * fz_hi;
+  const uint4 own = philox4x32_10(make_uint4(mx, my, mz, 0u), key);
+  const uint4 par = philox4x32_10(make_uint4(mx, py, pz_lo & (H - 1), 0u), key);
+  // partner words: the partner of mode lo is pz_lo (lo words if pz_lo < H)
+  const bool plo_is_lo = pz_lo < H;
+  float2 out[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int z = h ? mz + H : mz, pz = h ? pz_hi : pz_lo, q = h ? q_hi : q_lo;
+    const int lin = z * N + my, plin = pz * N + py;
+    const float a = __ldg(amp + q);
+    const float2 g_own = h ? box_muller(own.z, own.w) : box_muller(own.x, own.y);
+    if (lin == plin) {
+      out[h] = q == 0 ? make_float2(0.f, 0.f) : make_float2(a * 1.41421356237309505f * g_own.x, 0.f);
+    } else if (lin < plin) {
+      out[h] = make_float2(a * g_own.x, a * g_own.y);
+    } else {
+      const bool use_lo = (h == 0) == plo_is_lo;
+      const float2 g = use_lo ? box_muller(par.x, par.y) : box_muller(par.z, par.w);
+      out[h] = make_float2(a * g.x, -a * g.y);
+    }
   }
-  const bool canon = lin < plin;
-  const uint4 w = philox4x32_10(make_uint4(mx >> 1, canon ? my : py, canon ? mz : pz, 0u), key);
-  const float2 g = box_muller(w.x, w.y);          // mx is even on both planes
-  return make_float2(a * g.x, canon ? a * g.y : -a * g.y);
+  lo = out[0];
+  hi = out[1];
 }
 
-// Entry (m_x', m_y, m_z) of the packed half spectrum.
+// Entries (m_x', m_y, mz) and (m_x', m_y, mz + N/2) of the packed half spectrum.
 template <int N>
-__device__ __forceinline__ float2 draw_packed(int xp, int my, int mz, const float* __restrict__ amp,
-                                              uint2 key) {
+__device__ __forceinline__ void draw_packed_pair(int xp, int my, int mz, const float* __restrict__ amp,
+                                                 uint2 key, float2& lo, float2& hi) {
+  constexpr int H = N / 2;
   if (xp == 0) {
-    const float2 A = draw_hermitian<N>(0, my, mz, amp, key);
-    const float2 B = draw_hermitian<N>(N / 2, my, mz, amp, key);
-    return make_float2(A.x - B.y, A.y + B.x);
+    float2 A0, A1, B0, B1;
+    draw_hermitian_pair<N>(0, my, mz, amp, key, A0, A1);
+    draw_hermitian_pair<N>(H, my, mz, amp, key, B0, B1);
+    lo = make_float2(A0.x - B0.y, A0.y + B0.x);
+    hi = make_float2(A1.x - B1.y, A1.y + B1.x);
+    return;
   }
-  const int fy = my <= N / 2 ? my : my - N, fz = mz <= N / 2 ? mz : mz - N;
-  const int q = xp * xp + fy * fy + fz * fz;
-  const float a = __ldg(amp + q);
-  const uint4 w = philox4x32_10(make_uint4(xp >> 1, my, mz, 0u), key);
-  const float2 g = (xp & 1) ? box_muller(w.z, w.w) : box_muller(w.x, w.y);
-  return make_float2(a * g.x, a * g.y);
+  const int fy = my <= H ? my : my - N;
+  const int fz_hi = mz + H <= H ? mz + H : mz + H - N;
+  const int base = xp * xp + fy * fy;
+  const float a_lo = __ldg(amp + base + mz * mz), a_hi = __ldg(amp + base + fz_hi * fz_hi);
+  const uint4 w = philox4x32_10(make_uint4(xp, my, mz, 0u), key);
+  const float2 g0 = box_muller(w.x, w.y), g1 = box_muller(w.z, w.w);
+  lo = make_float2(a_lo * g0.x, a_lo * g0.y);
+  hi = make_float2(a_hi * g1.x, a_hi * g1.y);
 }
 
 template <int N, int R, int T>
@@ -69,26 +94,35 @@ __global__ void __launch_bounds__(T*(N / R)) k_draw_zfft(float2* __restrict__ bu
   const int my = blockIdx.y;
   float2 v[R];
 #pragma unroll
-  for (int r = 0; r < R; ++r) v[r] = draw_packed<N>(xp, my, j + r * NB, amp, key);
+  for (int r = 0; r < R / 2; ++r) draw_packed_pair<N>(xp, my, j + r * NB, amp, key, v[r], v[r + R / 2]);
   float2* col = buf + static_cast<size_t>(my) * N2 + xp;   // (z, my, xp) at col[z N N2]
   stockham<N, R, N, false>(
       v, sm, tw, j, [&](int n) { return n * T + c; },
       [&](int n, float2 x) { col[static_cast<size_t>(n) * N * N2] = x; }, BlockSync{});
 }
 
+// In-place inverse FFT along y of the T adjacent columns x0 .. x0+T-1 of one
+// z-plane (plane points at element (z, 0, 0)); blockDim.x == T * N / R.
+// Loads and stores go through L2 only (.cg), so the data may have been written
+// by other thread blocks of the same cluster.
 template <int N, int R, int T>
-__global__ void __launch_bounds__(T*(N / R)) k_yfft(float2* __restrict__ buf, const float2* __restrict__ tw) {
+__device__ __forceinline__ void yfft_tile(float2* __restrict__ plane, int x0, float2* sm,
+                                          const float2* __restrict__ tw) {
   constexpr int N2 = N / 2, NB = N / R;
-  extern __shared__ float2 sm[];
   const int c = threadIdx.x % T, j = threadIdx.x / T;
-  const int xp = blockIdx.x * T + c;
-  float2* col = buf + static_cast<size_t>(blockIdx.y) * N * N2 + xp;   // (z, y, xp) at col[y N2]
+  float2* col = plane + x0 + c;                                   // (y, x0 + c) at col[y N2]
   float2 v[R];
 #pragma unroll
-  for (int r = 0; r < R; ++r) v[r] = col[static_cast<size_t>(j + r * NB) * N2];
+  for (int r = 0; r < R; ++r) v[r] = __ldcg(col + static_cast<size_t>(j + r * NB) * N2);
   stockham<N, R, N, false>(
       v, sm, tw, j, [&](int n) { return n * T + c; },
-      [&](int n, float2 x) { col[static_cast<size_t>(n) * N2] = x; }, BlockSync{});
+      [&](int n, float2 x) { __stcg(col + static_cast<size_t>(n) * N2, x); }, BlockSync{});
+}
+
+template <int N, int R, int T>
+__global__ void __launch_bounds__(T*(N / R)) k_yfft(float2* __restrict__ buf, const float2* __restrict__ tw) {
+  extern __shared__ float2 sm[];
+  yfft_tile<N, R, T>(buf + static_cast<size_t>(blockIdx.y) * N * (N / 2), blockIdx.x * T, sm, tw);
 }
 
 // Row pass: for k in [0, N/2) the half-length input is
@@ -96,16 +130,18 @@ __global__ void __launch_bounds__(T*(N / R)) k_yfft(float2* __restrict__ buf, co
 // with G[0], G[N/2] the real and imaginary parts of the packed entry 0, so that
 // the N/2-point inverse FFT y[n] = f(2n) + i f(2n+1) is the real row itself.
 template <int N, int R, int ROWS>
-__global__ void __launch_bounds__(ROWS*(N / 2 / R)) k_xc2r(float2* __restrict__ buf, const float2* __restrict__ tw) {
+__device__ __forceinline__ void xc2r_rows(float2* __restrict__ rows, float2* sm, const float2* __restrict__ tw) {
   constexpr int N2 = N / 2, NB = N2 / R;
   constexpr int P = N2 + (N2 >> 4);            // row pitch: one pad slot per 16 entries
-  extern __shared__ float2 sm[];
   const int j = threadIdx.x % NB, rl = threadIdx.x / NB;
-  float2* g = buf + (static_cast<size_t>(blockIdx.x) * ROWS + rl) * N2;
+  float2* g = rows + static_cast<size_t>(rl) * N2;
   auto sidx = [&](int n) { return rl * P + n + (n >> 4); };
-  for (int i = j; i < N2; i += NB) sm[sidx(i)] = g[i];
-  __syncthreads();
   float2 v[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) v[r] = __ldcg(g + j + r * NB);     // all loads in flight at once
+#pragma unroll
+  for (int r = 0; r < R; ++r) sm[sidx(j + r * NB)] = v[r];
+  __syncthreads();
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const int k = j + r * NB;
@@ -118,6 +154,39 @@ __global__ void __launch_bounds__(ROWS*(N / 2 / R)) k_xc2r(float2* __restrict__ 
     }
   }
   stockham<N2, R, N, true>(v, sm, tw, j, sidx, [&](int n, float2 x) { g[n] = x; }, BlockSync{});
+}
+
+template <int N, int R, int ROWS>
+__global__ void __launch_bounds__(ROWS*(N / 2 / R)) k_xc2r(float2* __restrict__ buf, const float2* __restrict__ tw) {
+  extern __shared__ float2 sm[];
+  xc2r_rows<N, R, ROWS>(buf + static_cast<size_t>(blockIdx.x) * ROWS * (N / 2), sm, tw);
+}
+
+// Fused y + x passes: one thread-block cluster of C blocks owns one z-plane.
+// Its blocks first transform the plane's N/2 columns along y (tiles of T
+// columns, block b taking tiles b, b+C, ...), wait at the cluster barrier, and
+// then transform the plane's N rows along x (block b taking rows
+// [b N/C, (b+1) N/C)).  The y-transformed plane (4 N^2 bytes) is written and
+// re-read through L2 while few planes are in flight, so HBM sees one read and
+// one write of the box for both axes.
+template <int N, int RY, int T, int RX, int C>
+__global__ void __launch_bounds__(T*(N / RY)) k_yx_fused(float2* __restrict__ buf, const float2* __restrict__ tw) {
+  constexpr int N2 = N / 2, NT = T * (N / RY), NBX = N2 / RX, ROWS = NT / NBX;
+  static_assert(NT % NBX == 0 && (N / C) % ROWS == 0 && (N2 / T) % C == 0, "fused pass shape");
+  extern __shared__ float2 sm[];
+  const int crank = blockIdx.x % C;                 // rank in the (C,1,1) cluster
+  float2* plane = buf + static_cast<size_t>(blockIdx.x / C) * N * N2;
+  for (int tile = crank; tile < N2 / T; tile += C) {
+    yfft_tile<N, RY, T>(plane, tile * T, sm, tw);
+    __syncthreads();
+  }
+  __threadfence();
+  asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+  asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+  for (int r0 = crank * (N / C); r0 < (crank + 1) * (N / C); r0 += ROWS) {
+    xc2r_rows<N, RX, ROWS>(plane + static_cast<size_t>(r0) * N2, sm, tw);
+    __syncthreads();
+  }
 }
 
 template <int N, int R, int T>
@@ -140,10 +209,10 @@ cudaError_t run_yfft(float2* buf, const float2* tw, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int N, int R>
+template <int N, int R, int THREADS>
 cudaError_t run_xc2r(float2* buf, const float2* tw, cudaStream_t s) {
   constexpr int N2 = N / 2, NB = N2 / R;
-  constexpr int ROWS0 = 256 / NB > 0 ? 256 / NB : 1;
+  constexpr int ROWS0 = THREADS / NB > 0 ? THREADS / NB : 1;
   constexpr int ROWS = ROWS0 < N * N ? ROWS0 : N * N;
   constexpr int P = N2 + (N2 >> 4);
   const size_t smem = sizeof(float2) * P * ROWS;
@@ -154,20 +223,50 @@ cudaError_t run_xc2r(float2* buf, const float2* tw, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// Diagnostic: the packed half spectrum [m_z][m_y][m_x'] with no transform.
+// Diagnostic: the packed half spectrum [m_z][m_y][m_x'] with no transform;
+// one thread per mode pair (mz, mz + N/2).
 template <int N>
 __global__ void k_draw_only(float2* __restrict__ buf, const float* __restrict__ amp, uint2 key) {
   constexpr int N2 = N / 2;
   const size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= static_cast<size_t>(N) * N * N2) return;
-  const int xp = static_cast<int>(i % N2), my = static_cast<int>((i / N2) % N), mz = static_cast<int>(i / (static_cast<size_t>(N2) * N));
-  buf[i] = draw_packed<N>(xp, my, mz, amp, key);
+  if (i >= static_cast<size_t>(N2) * N * N2) return;
+  const int xp = static_cast<int>(i % N2), my = static_cast<int>((i / N2) % N);
+  const int mz = static_cast<int>(i / (static_cast<size_t>(N2) * N));
+  float2 lo, hi;
+  draw_packed_pair<N>(xp, my, mz, amp, key, lo, hi);
+  buf[(static_cast<size_t>(mz) * N + my) * N2 + xp] = lo;
+  buf[(static_cast<size_t>(mz + N2) * N + my) * N2 + xp] = hi;
 }
 
 template <int N>
 cudaError_t run_draw_only(float2* buf, const float* amp, uint2 key, cudaStream_t s) {
-  const size_t n = static_cast<size_t>(N) * N * (N / 2);
+  const size_t n = static_cast<size_t>(N / 2) * N * (N / 2);
   k_draw_only<N><<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(buf, amp, key);
+  return cudaGetLastError();
+}
+
+template <int N, int RY, int T, int RX, int C>
+cudaError_t run_yx_fused(float2* buf, const float2* tw, cudaStream_t s) {
+  constexpr int N2 = N / 2, NT = T * (N / RY), NBX = N2 / RX, ROWS = NT / NBX;
+  constexpr int P = N2 + (N2 >> 4);
+  constexpr size_t smem = sizeof(float2) * (N * T > ROWS * P ? N * T : ROWS * P);
+  auto kern = k_yx_fused<N, RY, T, RX, C>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(C * N);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, kern, buf, tw);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
@@ -177,21 +276,84 @@ inline uint2 key_of(uint64_t seed) {
 
 }  // namespace
 
-// Column-pass shapes (radix R, tile width T) and row-pass radix per box size.
-cudaError_t launch_draw_zfft(int N, float2* buf, const float* amp, const float2* tw, uint64_t seed,
+// ---------------------------------------------------------------------------
+// Variant tables.  Every box size has a default shape (variant 0); sizes from
+// 256 up have alternatives (radix, tile width, threads per block) that the
+// plan's autotuner times on the device.
+//   column passes (draw + z, y):  (R, T), T * N / R threads, N * T * 8 B shared
+//   row pass (x):                 (R, threads per block)
+//   fused y+x pass:               (RY, T, RX, cluster size C)
+// ---------------------------------------------------------------------------
+
+int num_col_variants(int N) { return N >= 256 ? 3 : 1; }
+int num_row_variants(int N) { return N >= 256 ? 3 : 1; }
+int num_fused_variants(int N) { return N == 128 ? 1 : (N == 256 || N == 512 || N == 1024) ? 2 : 0; }
+
+#define CMB3D_COL_SWITCH(RUN, ...)                                                        \
+  switch (N * 4 + v) {                                                                  \
+    case 8 * 4: return RUN<8, 8, 4>(__VA_ARGS__);                                          \
+    case 16 * 4: return RUN<16, 8, 8>(__VA_ARGS__);                                        \
+    case 32 * 4: return RUN<32, 8, 16>(__VA_ARGS__);                                       \
+    case 64 * 4: return RUN<64, 8, 16>(__VA_ARGS__);                                       \
+    case 128 * 4: return RUN<128, 8, 16>(__VA_ARGS__);                                     \
+    case 256 * 4: return RUN<256, 8, 16>(__VA_ARGS__);                                     \
+    case 256 * 4 + 1: return RUN<256, 16, 16>(__VA_ARGS__);                                \
+    case 256 * 4 + 2: return RUN<256, 8, 8>(__VA_ARGS__);                                  \
+    case 512 * 4: return RUN<512, 8, 16>(__VA_ARGS__);                                     \
+    case 512 * 4 + 1: return RUN<512, 16, 16>(__VA_ARGS__);                                \
+    case 512 * 4 + 2: return RUN<512, 8, 8>(__VA_ARGS__);                                  \
+    case 1024 * 4: return RUN<1024, 16, 16>(__VA_ARGS__);                                  \
+    case 1024 * 4 + 1: return RUN<1024, 16, 8>(__VA_ARGS__);                               \
+    case 1024 * 4 + 2: return RUN<1024, 8, 8>(__VA_ARGS__);                                \
+    case 2048 * 4: return RUN<2048, 16, 8>(__VA_ARGS__);                                   \
+    case 2048 * 4 + 1: return RUN<2048, 16, 4>(__VA_ARGS__);                               \
+    case 2048 * 4 + 2: return RUN<2048, 8, 4>(__VA_ARGS__);                                \
+    default: return cudaErrorInvalidValue;                                              \
+  }
+
+cudaError_t launch_draw_zfft(int N, int v, float2* buf, const float* amp, const float2* tw, uint64_t seed,
                              cudaStream_t s) {
   const uint2 key = key_of(seed);
-  switch (N) {
-    case 8: return run_draw_zfft<8, 8, 4>(buf, amp, tw, key, s);
-    case 16: return run_draw_zfft<16, 8, 8>(buf, amp, tw, key, s);
-    case 32: return run_draw_zfft<32, 8, 16>(buf, amp, tw, key, s);
-    case 64: return run_draw_zfft<64, 8, 16>(buf, amp, tw, key, s);
-    case 128: return run_draw_zfft<128, 8, 16>(buf, amp, tw, key, s);
-    case 256: return run_draw_zfft<256, 8, 16>(buf, amp, tw, key, s);
-    case 512: return run_draw_zfft<512, 8, 16>(buf, amp, tw, key, s);
-    case 1024: return run_draw_zfft<1024, 16, 16>(buf, amp, tw, key, s);
-    case 2048: return run_draw_zfft<2048, 16, 8>(buf, amp, tw, key, s);
+  CMB3D_COL_SWITCH(run_draw_zfft, buf, amp, tw, key, s)
+}
+
+cudaError_t launch_yfft(int N, int v, float2* buf, const float2* tw, cudaStream_t s) {
+  CMB3D_COL_SWITCH(run_yfft, buf, tw, s)
+}
+
+cudaError_t launch_xc2r(int N, int v, float2* buf, const float2* tw, cudaStream_t s) {
+  switch (N * 4 + v) {
+    case 8 * 4: return run_xc2r<8, 4, 256>(buf, tw, s);
+    case 16 * 4: return run_xc2r<16, 8, 256>(buf, tw, s);
+    case 32 * 4: return run_xc2r<32, 8, 256>(buf, tw, s);
+    case 64 * 4: return run_xc2r<64, 8, 256>(buf, tw, s);
+    case 128 * 4: return run_xc2r<128, 8, 256>(buf, tw, s);
+    case 256 * 4: return run_xc2r<256, 8, 256>(buf, tw, s);
+    case 256 * 4 + 1: return run_xc2r<256, 16, 256>(buf, tw, s);
+    case 256 * 4 + 2: return run_xc2r<256, 8, 512>(buf, tw, s);
+    case 512 * 4: return run_xc2r<512, 8, 256>(buf, tw, s);
+    case 512 * 4 + 1: return run_xc2r<512, 16, 256>(buf, tw, s);
+    case 512 * 4 + 2: return run_xc2r<512, 8, 512>(buf, tw, s);
+    case 1024 * 4: return run_xc2r<1024, 8, 256>(buf, tw, s);
+    case 1024 * 4 + 1: return run_xc2r<1024, 16, 256>(buf, tw, s);
+    case 1024 * 4 + 2: return run_xc2r<1024, 8, 512>(buf, tw, s);
+    case 2048 * 4: return run_xc2r<2048, 16, 256>(buf, tw, s);
+    case 2048 * 4 + 1: return run_xc2r<2048, 16, 512>(buf, tw, s);
+    case 2048 * 4 + 2: return run_xc2r<2048, 8, 512>(buf, tw, s);
     default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_yx_fused(int N, int v, float2* buf, const float2* tw, cudaStream_t s) {
+  switch (N * 4 + v) {
+    case 128 * 4: return run_yx_fused<128, 8, 16, 8, 4>(buf, tw, s);
+    case 256 * 4: return run_yx_fused<256, 8, 16, 8, 8>(buf, tw, s);
+    case 256 * 4 + 1: return run_yx_fused<256, 16, 16, 8, 8>(buf, tw, s);
+    case 512 * 4: return run_yx_fused<512, 8, 16, 8, 8>(buf, tw, s);
+    case 512 * 4 + 1: return run_yx_fused<512, 16, 16, 8, 8>(buf, tw, s);
+    case 1024 * 4: return run_yx_fused<1024, 16, 16, 8, 8>(buf, tw, s);
+    case 1024 * 4 + 1: return run_yx_fused<1024, 16, 8, 8, 8>(buf, tw, s);
+    default: return cudaErrorNotSupported;
   }
 }
 
@@ -207,36 +369,6 @@ cudaError_t launch_draw_only(int N, float2* buf, const float* amp, uint64_t seed
     case 512: return run_draw_only<512>(buf, amp, key, s);
     case 1024: return run_draw_only<1024>(buf, amp, key, s);
     case 2048: return run_draw_only<2048>(buf, amp, key, s);
-    default: return cudaErrorInvalidValue;
-  }
-}
-
-cudaError_t launch_yfft(int N, float2* buf, const float2* tw, cudaStream_t s) {
-  switch (N) {
-    case 8: return run_yfft<8, 8, 4>(buf, tw, s);
-    case 16: return run_yfft<16, 8, 8>(buf, tw, s);
-    case 32: return run_yfft<32, 8, 16>(buf, tw, s);
-    case 64: return run_yfft<64, 8, 16>(buf, tw, s);
-    case 128: return run_yfft<128, 8, 16>(buf, tw, s);
-    case 256: return run_yfft<256, 8, 16>(buf, tw, s);
-    case 512: return run_yfft<512, 8, 16>(buf, tw, s);
-    case 1024: return run_yfft<1024, 16, 16>(buf, tw, s);
-    case 2048: return run_yfft<2048, 16, 8>(buf, tw, s);
-    default: return cudaErrorInvalidValue;
-  }
-}
-
-cudaError_t launch_xc2r(int N, float2* buf, const float2* tw, cudaStream_t s) {
-  switch (N) {
-    case 8: return run_xc2r<8, 4>(buf, tw, s);
-    case 16: return run_xc2r<16, 8>(buf, tw, s);
-    case 32: return run_xc2r<32, 8>(buf, tw, s);
-    case 64: return run_xc2r<64, 8>(buf, tw, s);
-    case 128: return run_xc2r<128, 8>(buf, tw, s);
-    case 256: return run_xc2r<256, 8>(buf, tw, s);
-    case 512: return run_xc2r<512, 8>(buf, tw, s);
-    case 1024: return run_xc2r<1024, 8>(buf, tw, s);
-    case 2048: return run_xc2r<2048, 16>(buf, tw, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -13,17 +13,26 @@ namespace cmb3d {
 // Draw the Gaussian Fourier coefficients of realization key and inverse-FFT
 // every (m_y, m_x') column along z.  amp[q] = sqrt(P_box(q) / 2) for
 // q = m_x^2 + m_y^2 + m_z^2; tw[m] = exp(+2 pi i m / N), m < N.
-cudaError_t launch_draw_zfft(int N, float2* buf, const float* amp, const float2* tw,
+// Kernel shape variants: v in [0, num_*_variants(N)); variant 0 is the default.
+int num_col_variants(int N);
+int num_row_variants(int N);
+int num_fused_variants(int N);
+
+cudaError_t launch_draw_zfft(int N, int v, float2* buf, const float* amp, const float2* tw,
                              uint64_t seed, cudaStream_t s);
 
 // Diagnostic: the drawn packed half spectrum [m_z][m_y][m_x'], untransformed.
 cudaError_t launch_draw_only(int N, float2* buf, const float* amp, uint64_t seed, cudaStream_t s);
 
 // Inverse FFT of every (z, m_x') column along y, in place.
-cudaError_t launch_yfft(int N, float2* buf, const float2* tw, cudaStream_t s);
+cudaError_t launch_yfft(int N, int v, float2* buf, const float2* tw, cudaStream_t s);
+
+// Fused y and x passes (one thread-block cluster per z-plane, the plane kept in
+// L2 between the two axes); num_fused_variants(N) > 0 for 128 <= N <= 1024.
+cudaError_t launch_yx_fused(int N, int v, float2* buf, const float2* tw, cudaStream_t s);
 
 // Complex-to-real inverse FFT of every (z, y) row along x, in place.
-cudaError_t launch_xc2r(int N, float2* buf, const float2* tw, cudaStream_t s);
+cudaError_t launch_xc2r(int N, int v, float2* buf, const float2* tw, cudaStream_t s);
 
 // Interpolate the field float[z][y][x] at npix pixels.  tab[i] = (tx, ty, tz,
 // packed base cell) in gather order; out[perm[i]] receives pixel i (perm may

@@ -168,9 +168,9 @@ extern "C" int cmb3d_realize_sample_noalloc(int N, double L, double r, const dou
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   float2* box = reinterpret_cast<float2*>(base);
   const float2* tw = reinterpret_cast<const float2*>(base + kBoxBytes) + tw_offset(N);
-  cudaError_t e = cmb3d::launch_draw_zfft(N, box, amp_dev, tw, seed, s);
-  if (e == cudaSuccess) e = cmb3d::launch_yfft(N, box, tw, s);
-  if (e == cudaSuccess) e = cmb3d::launch_xc2r(N, box, tw, s);
+  cudaError_t e = cmb3d::launch_draw_zfft(N, 0, box, amp_dev, tw, seed, s);
+  if (e == cudaSuccess) e = cmb3d::launch_yfft(N, 0, box, tw, s);
+  if (e == cudaSuccess) e = cmb3d::launch_xc2r(N, 0, box, tw, s);
   if (e == cudaSuccess && npix > 0) {
     const unsigned blocks = static_cast<unsigned>((npix + 255) / 256);
     const float* field = reinterpret_cast<const float*>(box);

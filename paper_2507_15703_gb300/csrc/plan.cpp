@@ -6,6 +6,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <utility>
@@ -37,6 +39,12 @@ struct TimingRec {
 
 constexpr size_t kMaxTimingRecs = 1 << 16;
 
+// Kernel shapes of one realization: variant of the draw+z pass, of the y and
+// x passes, or of the fused y+x pass (fused < 0: separate y and x passes).
+struct Schedule {
+  int draw = 0, y = 0, x = 0, fused = -1;
+};
+
 }  // namespace
 
 struct cmb3d_plan_s {
@@ -57,6 +65,8 @@ struct cmb3d_plan_s {
   std::vector<double> knodes, pnodes;
   std::vector<TimingRec> recs;
   size_t tnext = 0;
+  Schedule sched;
+  bool tuned = false;
 };
 
 namespace {
@@ -129,14 +139,102 @@ cudaError_t timed(cmb3d_plan_s* p, int stage, cudaStream_t s, F f) {
   return cudaEventRecord(r.b, s);
 }
 
-// The three FFT passes (draw fused into the first), leaving the real field in buf.
+// Autotuner: time every kernel variant of this box size once (1 warm-up and
+// 3 timed launches each, CUDA events on the caller's stream) and keep the
+// fastest draw, y and x variants and, where available, the fastest fused y+x
+// variant if it beats the best separate pair.  Results are cached per
+// (device, N, flag restriction) for the life of the process.
+std::mutex g_tune_mu;
+std::map<std::pair<int, int>, Schedule> g_tune_cache;
+
+template <class F>
+float time_launches(cudaStream_t s, F f, bool* ok) {
+  cudaEvent_t a, b;
+  if (cudaEventCreate(&a) != cudaSuccess) {
+    *ok = false;
+    return 0.f;
+  }
+  if (cudaEventCreate(&b) != cudaSuccess) {
+    cudaEventDestroy(a);
+    *ok = false;
+    return 0.f;
+  }
+  float ms = 0.f;
+  *ok = f() == cudaSuccess && cudaEventRecord(a, s) == cudaSuccess;
+  for (int i = 0; i < 3 && *ok; ++i) *ok = f() == cudaSuccess;
+  *ok = *ok && cudaEventRecord(b, s) == cudaSuccess && cudaEventSynchronize(b) == cudaSuccess &&
+        cudaEventElapsedTime(&ms, a, b) == cudaSuccess;
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (!*ok) cudaGetLastError();
+  return ms / 3.f;
+}
+
+int autotune(cmb3d_plan_s* p, cudaStream_t s) {
+  const int N = p->N;
+  const int restrict_bits = p->flags & (CMB3D_FLAG_THREE_PASS | CMB3D_FLAG_FUSED_YX);
+  const std::pair<int, int> key(p->device, N * 16 + restrict_bits);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      p->sched = it->second;
+      p->tuned = true;
+      return CMB3D_OK;
+    }
+  }
+  Schedule best;
+  bool ok = true;
+  float t_best = 1e30f;
+  for (int v = 0; v < cmb3d::num_col_variants(N); ++v) {
+    const float t = time_launches(s, [&] { return cmb3d::launch_draw_zfft(N, v, p->buf, p->amp, p->tw, 1, s); }, &ok);
+    if (!ok) return fail_cuda(cudaErrorLaunchFailure, "autotune draw_zfft");
+    if (t < t_best) t_best = t, best.draw = v;
+  }
+  float t_y = 1e30f, t_x = 1e30f, t_f = 1e30f;
+  for (int v = 0; v < cmb3d::num_col_variants(N); ++v) {
+    const float t = time_launches(s, [&] { return cmb3d::launch_yfft(N, v, p->buf, p->tw, s); }, &ok);
+    if (!ok) return fail_cuda(cudaErrorLaunchFailure, "autotune yfft");
+    if (t < t_y) t_y = t, best.y = v;
+  }
+  for (int v = 0; v < cmb3d::num_row_variants(N); ++v) {
+    const float t = time_launches(s, [&] { return cmb3d::launch_xc2r(N, v, p->buf, p->tw, s); }, &ok);
+    if (!ok) return fail_cuda(cudaErrorLaunchFailure, "autotune xc2r");
+    if (t < t_x) t_x = t, best.x = v;
+  }
+  if (!(p->flags & CMB3D_FLAG_THREE_PASS))
+    for (int v = 0; v < cmb3d::num_fused_variants(N); ++v) {
+      const float t = time_launches(s, [&] { return cmb3d::launch_yx_fused(N, v, p->buf, p->tw, s); }, &ok);
+      if (!ok) return fail_cuda(cudaErrorLaunchFailure, "autotune yx_fused");
+      if (t < t_f) t_f = t, best.fused = v;
+    }
+  if (!(p->flags & CMB3D_FLAG_FUSED_YX) && t_y + t_x <= t_f) best.fused = -1;
+  p->sched = best;
+  p->tuned = true;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune_cache[key] = best;
+  return CMB3D_OK;
+}
+
+// The FFT passes (draw fused into the first), leaving the real field in buf.
 int run_field(cmb3d_plan_s* p, uint64_t seed, cudaStream_t s) {
+  if ((p->flags & CMB3D_FLAG_AUTOTUNE) && !p->tuned) {
+    int st = autotune(p, s);
+    if (st != CMB3D_OK) return st;
+  }
+  const Schedule& sc = p->sched;
   cudaError_t e;
-  e = timed(p, CMB3D_STAGE_DRAW_ZFFT, s, [&] { return cmb3d::launch_draw_zfft(p->N, p->buf, p->amp, p->tw, seed, s); });
+  e = timed(p, CMB3D_STAGE_DRAW_ZFFT, s,
+            [&] { return cmb3d::launch_draw_zfft(p->N, sc.draw, p->buf, p->amp, p->tw, seed, s); });
   if (e != cudaSuccess) return fail_cuda(e, "draw_zfft launch");
-  e = timed(p, CMB3D_STAGE_YFFT, s, [&] { return cmb3d::launch_yfft(p->N, p->buf, p->tw, s); });
+  if (sc.fused >= 0) {
+    e = timed(p, CMB3D_STAGE_YX_FUSED, s, [&] { return cmb3d::launch_yx_fused(p->N, sc.fused, p->buf, p->tw, s); });
+    if (e != cudaSuccess) return fail_cuda(e, "yx_fused launch");
+    return CMB3D_OK;
+  }
+  e = timed(p, CMB3D_STAGE_YFFT, s, [&] { return cmb3d::launch_yfft(p->N, sc.y, p->buf, p->tw, s); });
   if (e != cudaSuccess) return fail_cuda(e, "yfft launch");
-  e = timed(p, CMB3D_STAGE_XC2R, s, [&] { return cmb3d::launch_xc2r(p->N, p->buf, p->tw, s); });
+  e = timed(p, CMB3D_STAGE_XC2R, s, [&] { return cmb3d::launch_xc2r(p->N, sc.x, p->buf, p->tw, s); });
   if (e != cudaSuccess) return fail_cuda(e, "xc2r launch");
   return CMB3D_OK;
 }
@@ -186,8 +284,11 @@ int cmb3d_plan(cmb3d_plan_t* out, int N, double L, double r, const double* pix_x
   if (npix < 0 || npix >= (int64_t(1) << 31)) return fail(CMB3D_EINVAL, "npix out of range");
   if (npix > 0 && !pix_xyz) return fail(CMB3D_EINVAL, "pix_xyz is NULL");
   if (interp != CMB3D_TRILINEAR && interp != CMB3D_TRICUBIC) return fail(CMB3D_EINVAL, "interp must be 1 or 3");
-  if (flags & ~uint32_t(CMB3D_FLAG_NO_SORT | CMB3D_FLAG_ALLOW_WRAP | CMB3D_FLAG_STAGE_TIMING))
+  if (flags & ~uint32_t(CMB3D_FLAG_NO_SORT | CMB3D_FLAG_ALLOW_WRAP | CMB3D_FLAG_STAGE_TIMING | CMB3D_FLAG_THREE_PASS |
+                        CMB3D_FLAG_FUSED_YX | CMB3D_FLAG_AUTOTUNE))
     return fail(CMB3D_EINVAL, "unknown flag bits");
+  if ((flags & CMB3D_FLAG_THREE_PASS) && (flags & CMB3D_FLAG_FUSED_YX))
+    return fail(CMB3D_EINVAL, "CMB3D_FLAG_THREE_PASS and CMB3D_FLAG_FUSED_YX exclude each other");
   for (int64_t i = 0; i < 3 * npix; ++i)
     if (!std::isfinite(pix_xyz[i])) return fail(CMB3D_EINVAL, "pixel coordinates must be finite");
 
@@ -199,6 +300,7 @@ int cmb3d_plan(cmb3d_plan_t* out, int N, double L, double r, const double* pix_x
   p->interp = interp;
   p->flags = flags;
   p->npix = npix;
+  if ((flags & CMB3D_FLAG_FUSED_YX) && cmb3d::num_fused_variants(N) > 0) p->sched.fused = 0;
   if (cudaGetDevice(&p->device) != cudaSuccess) {
     cudaGetLastError();
     delete p;
@@ -475,6 +577,39 @@ int cmb3d_stage_times(cmb3d_plan_t p, double* ms, int64_t* launches, int n, int 
     if (launches) launches[i] = i < CMB3D_NUM_STAGES ? cnt[static_cast<size_t>(i)] : 0;
   }
   if (reset) p->tnext = 0;
+  return CMB3D_OK;
+}
+
+int cmb3d_plan_schedule(cmb3d_plan_t p, int* sched) {
+  if (!p || !sched) return fail(CMB3D_EINVAL, "plan or sched is NULL");
+  sched[0] = p->sched.draw;
+  sched[1] = p->sched.fused >= 0 ? -1 : p->sched.y;
+  sched[2] = p->sched.fused >= 0 ? -1 : p->sched.x;
+  sched[3] = p->sched.fused;
+  return CMB3D_OK;
+}
+
+int cmb3d_plan_set_schedule(cmb3d_plan_t p, const int* sched) {
+  if (!p || !sched) return fail(CMB3D_EINVAL, "plan or sched is NULL");
+  const int N = p->N;
+  Schedule sc;
+  sc.draw = sched[0];
+  sc.fused = sched[3];
+  if (sc.draw < 0 || sc.draw >= cmb3d::num_col_variants(N)) return fail(CMB3D_EINVAL, "draw variant out of range");
+  if (sc.fused >= 0) {
+    if (sc.fused >= cmb3d::num_fused_variants(N)) return fail(CMB3D_EINVAL, "fused variant out of range");
+    if (p->flags & CMB3D_FLAG_THREE_PASS) return fail(CMB3D_EINVAL, "plan is restricted to separate passes");
+  } else {
+    sc.fused = -1;
+    sc.y = sched[1];
+    sc.x = sched[2];
+    if (sc.y < 0 || sc.y >= cmb3d::num_col_variants(N)) return fail(CMB3D_EINVAL, "y variant out of range");
+    if (sc.x < 0 || sc.x >= cmb3d::num_row_variants(N)) return fail(CMB3D_EINVAL, "x variant out of range");
+    if (p->flags & CMB3D_FLAG_FUSED_YX && cmb3d::num_fused_variants(N) > 0)
+      return fail(CMB3D_EINVAL, "plan is restricted to the fused pass");
+  }
+  p->sched = sc;
+  p->tuned = true;
   return CMB3D_OK;
 }
 

@@ -90,6 +90,67 @@ def test_field_matches_oracle(N):
     assert rel_err(got, ref) <= TOL
 
 
+@pytest.mark.parametrize("N", [128, 256, 512, 1024])
+def test_fused_yx_pass_matches_three_pass_and_oracle(N):
+    """The cluster-fused y+x pass (default shape) gives the same field, bit for
+    bit, as the separate passes of the same radices, and matches the oracle."""
+    L = 2.2
+    kn, pk = smooth_pk(N, L)
+    pix = fibonacci_sphere(20000, 4999)
+    flags = cmb3d.CMB3D_FLAG_STAGE_TIMING
+    with cmb3d.Plan(N, L, 1.0, pix, 3, flags | cmb3d.CMB3D_FLAG_FUSED_YX) as fused, \
+            cmb3d.Plan(N, L, 1.0, pix, 3, flags | cmb3d.CMB3D_FLAG_THREE_PASS) as three:
+        fused.set_pk(kn, pk)
+        three.set_pk(kn, pk)
+        assert cmb3d.cmb3d_plan_schedule(fused.handle) == (0, -1, -1, 0)
+        a = fused.realize_sample(3).cpu().numpy()
+        b = three.realize_sample(3).cpu().numpy()
+        np.testing.assert_array_equal(a, b)
+        _, cf = cmb3d.cmb3d_stage_times(fused.handle)
+        _, ct = cmb3d.cmb3d_stage_times(three.handle)
+        assert list(cf) == [1, 0, 0, 1, 1] and list(ct) == [1, 1, 1, 1, 0]
+        if N <= 256:
+            fa = fused.realize_field(5).cpu().numpy()
+            ref = orc.realize_field(N, orc.p_box_of_q(N, L, kn, pk), 5)
+            assert rel_err(fa, ref) <= TOL
+    if N <= 512:
+        ref = orc.realize_sample(N, L, 1.0, pix, orc.p_box_of_q(N, L, kn, pk), 3, 3)
+        assert rel_err(a, ref) <= TOL
+
+
+@pytest.mark.parametrize("N", [256, 512])
+def test_every_kernel_variant_matches_oracle(N):
+    """Each radix / tile / thread-count variant the autotuner may pick."""
+    L = 2.2
+    kn, pk = smooth_pk(N, L)
+    pix = fibonacci_sphere(20000, 6007)
+    ref = orc.realize_sample(N, L, 1.0, pix, orc.p_box_of_q(N, L, kn, pk), 17, 3)
+    scheds = [(d, 0, 0, -1) for d in range(3)] + [(0, y, 0, -1) for y in range(3)] + \
+             [(0, 0, x, -1) for x in range(3)] + [(0, -1, -1, f) for f in range(2)]
+    with cmb3d.Plan(N, L, 1.0, pix, 3) as plan:
+        plan.set_pk(kn, pk)
+        for sc in scheds:
+            cmb3d.cmb3d_plan_set_schedule(plan.handle, sc)
+            assert cmb3d.cmb3d_plan_schedule(plan.handle) == sc
+            got = plan.realize_sample(17).cpu().numpy()
+            assert rel_err(got, ref) <= TOL, sc
+        with pytest.raises(cmb3d.Cmb3dError):
+            cmb3d.cmb3d_plan_set_schedule(plan.handle, (3, 0, 0, -1))
+
+
+def test_autotune_picks_valid_schedule():
+    N, L = 256, 2.2
+    kn, pk = smooth_pk(N, L)
+    pix = fibonacci_sphere(20000, 3001)
+    with cmb3d.Plan(N, L, 1.0, pix, 3, cmb3d.CMB3D_FLAG_AUTOTUNE) as plan:
+        plan.set_pk(kn, pk)
+        got = plan.realize_sample(2).cpu().numpy()
+        d, y, x, f = cmb3d.cmb3d_plan_schedule(plan.handle)
+        assert 0 <= d < 3 and ((f >= 0 and y == x == -1) or (f == -1 and 0 <= y < 3 and 0 <= x < 3))
+    ref = orc.realize_sample(N, L, 1.0, pix, orc.p_box_of_q(N, L, kn, pk), 2, 3)
+    assert rel_err(got, ref) <= TOL
+
+
 def oracle_pk_for(w):
     ell, cl = w.cl()
     kn, pk, _ = orc.invert_cl(ell, cl, w.N, w.L, w.r, w.nkbins)
@@ -196,9 +257,9 @@ def test_host_batch_and_timing_paths_agree():
         np.testing.assert_array_equal(oa.cpu().numpy(), da)
         np.testing.assert_array_equal(ob.cpu().numpy(), db)
         ms, cnt = cmb3d.cmb3d_stage_times(a.handle)
-        assert list(cnt) == [3, 3, 3, 3] and np.all(ms > 0)
+        assert list(cnt) == [3, 3, 3, 3, 0] and np.all(ms[:4] > 0)
         ms2, cnt2 = cmb3d.cmb3d_stage_times(a.handle)
-        assert list(cnt2) == [0, 0, 0, 0]
+        assert list(cnt2) == [0, 0, 0, 0, 0]
 
 
 def test_box_variance_over_seeds():
