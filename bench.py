@@ -136,6 +136,7 @@ KERNEL_SOURCES = {
     "xc2r": ["paper_2507_15703_gb300/csrc/fft_passes.cu", "paper_2507_15703_gb300/csrc/device_common.cuh"],
     "gather": ["paper_2507_15703_gb300/csrc/gather.cu"],
     "yx_fused": ["paper_2507_15703_gb300/csrc/fft_passes.cu", "paper_2507_15703_gb300/csrc/device_common.cuh"],
+    "batch": ["paper_2507_15703_gb300/csrc/batch.cu", "paper_2507_15703_gb300/csrc/fft_tiles.cuh"],
 }
 
 
@@ -174,6 +175,8 @@ def run_cuda(args, rank, world, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     w = WORKLOADS[args.workload]
+    if w.batch > 1:
+        return run_cuda_batch(args, rank, world, local, w)
     pix = w.pixels()
     npix = pix.shape[0]
     ell, cl = w.cl()
@@ -191,10 +194,7 @@ def run_cuda(args, rank, world, local):
     out = torch.empty(npix, dtype=torch.float32, device=dev)
     seed0 = 1000003 * rank
 
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
+    dist = init_dist(world, dev)
 
     def barrier():
         if dist is not None:
@@ -223,12 +223,7 @@ def run_cuda(args, rank, world, local):
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
     stage_ms, stage_n = cmb3d.cmb3d_stage_times(plan.handle, reset=True)
-
-    t_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
+    t_max = max_over_ranks(dist, ms, dev)
 
     # end to end through the host-buffer entry point (map copied to pinned host memory)
     host = torch.empty(npix, dtype=torch.float32).pin_memory().numpy()
@@ -238,37 +233,169 @@ def run_cuda(args, rank, world, local):
     for i in range(args.steps):
         cmb3d.cmb3d_realize_sample_to_host(plan.handle, seed0 + i, host, stream)
     barrier()
-    e2e_s = time.perf_counter() - t1
-    if dist is not None:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(dist, time.perf_counter() - t1, dev)
     cmb3d.cmb3d_stage_times(plan.handle, reset=True)
     plan.close()
 
     if rank != 0:
-        if dist is not None:
-            dist.destroy_process_group()
+        finish_dist(dist)
         return
 
     maps = world * args.steps
     value = maps / (t_max / 1e3)
     ab = algorithmic_bytes(w.N, npix)
     names = cmb3d.STAGE_NAMES
-    peak, peak_kind = measured_peaks()
     kernels = {}
     for i, name in enumerate(names):
         n = int(stage_n[i])
         if n == 0:
             continue
-        avg_ms = stage_ms[i] / max(n, 1)
-        gbs = ab[name] / (avg_ms / 1e3) / 1e9 if n else None
-        kernels[name] = {"launches": n, "avg_ms": round(avg_ms, 5), "share": round(stage_ms[i] / max(stage_ms.sum(), 1e-12), 4),
-                         "alg_bytes": ab[name], "alg_gbs": round(gbs, 1) if gbs else None,
-                         "frac_of_measured_hbm": round(gbs / peak, 4) if gbs else None}
+        kernels[name] = kernel_entry(n, stage_ms[i], stage_ms.sum(), ab[name])
     dom = names[int(np.argmax(stage_ms))]
+    per_map_bytes = sum(ab[k] for k in kernels)
+    config = {"workload": args.workload, "N": w.N, "L_over_r": w.L_over_r, "npix": npix, "fsky": w.fsky,
+              "interp": "tricubic" if w.interp == 3 else "trilinear", "lmax": w.lmax, "nkbins": w.nkbins,
+              "parallelism": f"replicas x{world}",
+              "schedule": {"draw": schedule[0], "y": schedule[1], "x": schedule[2], "fused_yx": schedule[3],
+                           "restriction": "three-pass" if args.three_pass else "fused" if args.fused else "autotuned"},
+              "l2": f"no flush: per-map working set {per_map_bytes / 2**30:.2f} GiB > 129 MiB L2",
+              "cl_fit_max_rel_err": fit_err, "plan_setup_s": round(setup_s, 2)}
+    emit(args, w, value, t_max, world, config, per_map_bytes, kernels, dom, maps / e2e_s, 4 * npix,
+         int(stage_n.sum()), clk)
+    finish_dist(dist)
+
+
+def run_cuda_batch(args, rank, world, local, w):
+    """Batched workload: one step = B maps (each box its own pixel set) in one
+    persistent launch replayed from a CUDA graph."""
+    import torch
+    from paper_2507_15703_gb300 import cmb3d
+
+    dev = torch.device("cuda", local)
+    pixs = w.batch_pixels()
+    ell, cl = w.cl()
+    t0 = time.time()
+    plans = [cmb3d.Plan(w.N, w.L, w.r, p, w.interp, cmb3d.CMB3D_FLAG_AUTOTUNE) for p in pixs]
+    fit_err = plans[0].set_cl(ell, cl, w.nkbins)
+    kn = np.linspace(0.0, math.sqrt(3) * math.pi * w.N / w.L, w.nkbins)
+    pk = cmb3d.cmb3d_get_pk(plans[0].handle, kn)
+    for p in plans[1:]:
+        p.set_pk(kn, pk)
+    setup_s = time.time() - t0
+    handles = [p.handle for p in plans]
+    npix = [p.shape[0] for p in pixs]
+    outs = [torch.empty(n, dtype=torch.float32, device=dev) for n in npix]
+    stream = torch.cuda.current_stream(dev)
+    dist = init_dist(world, dev)
+    base = 1000003 * rank
+
+    def step(i):
+        cmb3d.cmb3d_realize_sample_batch(handles, [base + i * w.batch + b for b in range(w.batch)], outs, stream)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for i in range(args.steps):
+        step(args.warmup + i)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    t_max = max_over_ranks(dist, ms, dev)
+
+    form, variant = cmb3d.cmb3d_batch_schedule(handles[0])
+    form_name = {0: f"persistent kernel ({2 - variant} blocks/SM) in a CUDA graph",
+                 1: "two-stream CUDA graph (draws || passes)"}.get(form, "none")
+
+    # the plain form for comparison: the same boxes realized one after another
+    for i in range(2):
+        for b, p in enumerate(plans):
+            cmb3d.cmb3d_realize_sample(handles[b], base + b, outs[b], stream)
+    torch.cuda.synchronize(dev)
+    pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    plain_steps = max(1, min(args.steps, 5))
+    pe0.record(stream)
+    for i in range(plain_steps):
+        for b, p in enumerate(plans):
+            cmb3d.cmb3d_realize_sample(handles[b], base + i * w.batch + b, outs[b], stream)
+    pe1.record(stream)
+    torch.cuda.synchronize(dev)
+    plain_value = plain_steps * w.batch / (pe0.elapsed_time(pe1) / 1e3)
+
+    # end to end: the same batches with every map copied to pinned host memory
+    hosts = [torch.empty(n, dtype=torch.float32).pin_memory() for n in npix]
+    torch.cuda.synchronize(dev)
+    t1 = time.perf_counter()
+    for i in range(args.steps):
+        step(i)
+        for h, o in zip(hosts, outs):
+            h.copy_(o, non_blocking=True)
+        torch.cuda.synchronize(dev)
+    e2e_s = max_over_ranks(dist, time.perf_counter() - t1, dev)
+    for p in plans:
+        p.close()
+    if rank != 0:
+        finish_dist(dist)
+        return
+    maps = world * args.steps * w.batch
+    value = maps / (t_max / 1e3)
+    ab = algorithmic_bytes(w.N, 0)
+    batch_bytes = w.batch * (ab["draw_zfft"] + ab["yfft"] + ab["xc2r"]) + 24 * sum(npix)
+    kernels = {"batch": kernel_entry(args.steps, ms, ms, batch_bytes)}
+    kernels["batch"]["note"] = "one step = the whole batch (persistent kernel or graph), CUDA events"
+    config = {"workload": args.workload, "N": w.N, "boxes_per_step": w.batch, "npix_total": int(sum(npix)),
+              "npix_min": int(min(npix)), "npix_max": int(max(npix)), "fsky": "U[0.05, 0.5] per box",
+              "interp": "tricubic" if w.interp == 3 else "trilinear", "lmax": w.lmax, "nkbins": w.nkbins,
+              "parallelism": f"replicas x{world}", "schedule": f"autotuned: {form_name}",
+              "l2": f"no flush: per-step working set {batch_bytes / 2**30:.1f} GiB > 129 MiB L2",
+              "cl_fit_max_rel_err": fit_err, "plan_setup_s": round(setup_s, 2),
+              "plain_form_maps_per_s": round(plain_value, 1)}
+    emit(args, w, value, t_max, world, config, batch_bytes / w.batch, kernels, "batch", maps / e2e_s,
+         4 * sum(npix), 2 * args.steps, clk)
+    finish_dist(dist)
+
+
+def init_dist(world, dev):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    dist.init_process_group("nccl", device_id=dev)
+    return dist
+
+
+def finish_dist(dist):
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def max_over_ranks(dist, v, dev):
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def kernel_entry(n, total_ms, all_ms, alg_bytes):
+    peak, _ = measured_peaks()
+    avg_ms = total_ms / max(n, 1)
+    gbs = alg_bytes / (avg_ms / 1e3) / 1e9
+    return {"launches": int(n), "avg_ms": round(float(avg_ms), 5), "share": round(float(total_ms / max(all_ms, 1e-12)), 4),
+            "alg_bytes": int(alg_bytes), "alg_gbs": round(gbs, 1), "frac_of_measured_hbm": round(gbs / peak, 4)}
+
+
+def emit(args, w, value, t_max, world, config, per_map_bytes, kernels, dom, e2e_value, d2h_bytes, launches, clk):
+    peak, peak_kind = measured_peaks()
     dk = kernels[dom]
-    per_map_bytes = sum(ab.values())
     line = {
         "metric": METRIC,
         "value": round(value, 3),
@@ -282,28 +409,20 @@ def run_cuda(args, rank, world, local):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic: Fibonacci-grid polar cap pixels, C_l family inverted to P(k) by the library's NNLS",
-        "config": {"workload": args.workload, "N": w.N, "L_over_r": w.L_over_r, "npix": npix, "fsky": w.fsky,
-                   "interp": "tricubic" if w.interp == 3 else "trilinear", "lmax": w.lmax, "nkbins": w.nkbins,
-                   "parallelism": f"replicas x{world}",
-                   "schedule": {"draw": schedule[0], "y": schedule[1], "x": schedule[2], "fused_yx": schedule[3],
-                                "restriction": "three-pass" if args.three_pass else "fused" if args.fused else "autotuned"},
-                   "l2": f"no flush: per-map working set {per_map_bytes / 2**30:.2f} GiB > 129 MiB L2",
-                   "cl_fit_max_rel_err": fit_err, "plan_setup_s": round(setup_s, 2)},
+        "config": config,
         "achieved_gbs_alg_per_map": round(per_map_bytes * value / world / 1e9, 1),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": dk["alg_gbs"], "peak": peak, "unit": "GB/s",
                      "frac": dk["frac_of_measured_hbm"], "peak_source": peak_kind,
                      "traffic": ncu_traffic(dom, args.workload)},
         "kernels": kernels,
-        "e2e": {"value": round(maps / e2e_s, 3), "unit": "maps/s", "h2d_bytes_per_step": 0,
-                "d2h_bytes_per_step": 4 * npix},
-        "gpu_launches": int(stage_n.sum()),
+        "e2e": {"value": round(e2e_value, 3), "unit": "maps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": int(d2h_bytes)},
+        "gpu_launches": int(launches),
         "clocks": clk,
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, args)
     print(json.dumps(line), flush=True)
-    if dist is not None:
-        dist.destroy_process_group()
 
 
 def sweep(plan, out, stream, N, seed0, reps=20):
@@ -340,7 +459,7 @@ def oracle_map_sample(w, seed):
     k = np.linspace(0.0, math.sqrt(3) * math.pi * w.N / w.L, w.nkbins)
     pk = 1e-3 / (1.0 + (k / 12.0) ** 3)
     pb = orc.p_box_of_q(w.N, w.L, k, pk)
-    pix = w.pixels()
+    pix = w.batch_pixels()[seed % w.batch] if w.batch > 1 else w.pixels()
     t = time.perf_counter()
     vals = orc.realize_sample(w.N, w.L, w.r, pix, pb, seed, w.interp)
     return time.perf_counter() - t, vals.size

@@ -178,16 +178,40 @@ int cmb3d_realize_sample_to_host(cmb3d_plan_t plan, uint64_t seed, float* out_ho
                                  void* stream);
 
 /*
- * Many maps at once (batched form of Sec. II.D.1; the paper notes that one set
- * of precomputed quantities serves many simulations, Sec. II.D.2, a remark that holds for the 3-D method too).
- *   plans     host array of B plans that share N, L and interp (their pixel
- *             sets and spectra may differ).
+ * Many maps at once (batched form of Sec. II.D.1; the paper generates batches
+ * of maps that reuse one set of precomputed quantities, Sec. II.D.2, Sec. IV).
+ *   plans     host array of B distinct plans that share N, L, interp and
+ *             device (their pixel sets and spectra may differ); each plan's
+ *             box holds its realization.
  *   seeds     host array of B seeds; outs_dev host array of B device pointers,
- *             each to that plan's npix floats.
- * Errors: CMB3D_EINVAL if the plans differ in N, L or interp.
+ *             each to that plan's npix floats (caller's pixel order).
+ * For N = 256 and 512 all B maps run in one persistent kernel launch, captured
+ * once in a CUDA graph (kept in plans[0] for that plan set) and replayed: the
+ * draw of one box overlaps with the FFT passes and gather of earlier ones.
+ * With CMB3D_FLAG_AUTOTUNE on plans[0] the first call also times the
+ * alternative form, a CUDA graph of two streams (draws on one, each box's
+ * passes on a higher-priority one), and keeps the faster for this plan set and
+ * these outputs.  Other N run the plans one after another.  Synchronises the stream before
+ * returning.  Errors: CMB3D_EINVAL if the plans differ in N, L, interp or
+ * device or repeat; CMB3D_ETIMEOUT if a bounded wait inside the persistent
+ * kernel gave up (the context stays usable); CMB3D_ECUDA.  Batches that share
+ * plans[0] must not run concurrently.
  */
 int cmb3d_realize_sample_batch(const cmb3d_plan_t* plans, const uint64_t* seeds,
                                float* const* outs_dev, int B, void* stream);
+
+/*
+ * Test controls of the batched path (process-wide):
+ *   spin_limit     polls of each bounded wait in the persistent kernel before
+ *                  it gives up (0 restores the default, about 2 s);
+ *   withhold_draw  != 0: draw items never report completion, so the waits that
+ *                  depend on them must time out (fault injection);
+ *   force_form     -1: the plan's choice; 0, 1: persistent kernel with two or
+ *                  one resident blocks per SM; 2: the two-stream CUDA graph
+ *                  (each box's draw on one stream, its y, x and gather passes
+ *                  on a higher-priority stream).
+ */
+void cmb3d_batch_debug(uint32_t spin_limit, int withhold_draw, int force_form);
 
 /*
  * Diagnostics of the intermediate stages of one realization (same seed
@@ -263,6 +287,13 @@ int cmb3d_plan_schedule(cmb3d_plan_t plan, int* sched);
  * plan's flags exclude.  sched: host array of 4 ints.
  */
 int cmb3d_plan_set_schedule(cmb3d_plan_t plan, const int* sched);
+
+/*
+ * The batched form last built with `plan` as plans[0]: *form = -1 (none), 0
+ * (persistent kernel; *variant = 0 two or 1 one resident blocks per SM) or 1
+ * (two-stream CUDA graph).  form, variant: host pointers.
+ */
+int cmb3d_batch_schedule(cmb3d_plan_t plan, int* form, int* variant);
 
 /* Plan properties: N, number of pixels, and device bytes owned by the plan. */
 int cmb3d_plan_info(cmb3d_plan_t plan, int* N, int64_t* npix, int64_t* device_bytes);

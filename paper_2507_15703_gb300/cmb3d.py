@@ -61,6 +61,7 @@ PROTOTYPES = {
     "cmb3d_realize_sample": (_i32, [_vp, _u64, _vp, _vp]),
     "cmb3d_realize_sample_to_host": (_i32, [_vp, _u64, _vp, _vp]),
     "cmb3d_realize_sample_batch": (_i32, [C.POINTER(_vp), C.POINTER(_u64), C.POINTER(_vp), _i32, _vp]),
+    "cmb3d_batch_debug": (None, [_u32, _i32, _i32]),
     "cmb3d_draw_spectrum": (_i32, [_vp, _u64, _vp, _vp]),
     "cmb3d_realize_field": (_i32, [_vp, _u64, _vp, _vp]),
     "cmb3d_philox4x32_10": (_i32, [_vp, _u64, _vp, _i64, _vp]),
@@ -68,6 +69,7 @@ PROTOTYPES = {
     "cmb3d_realize_sample_noalloc": (_i32, [_i32, C.c_double, C.c_double, _vp, _i64, _i32, _vp, _u64, _vp, _vp]),
     "cmb3d_plan_info": (_i32, [_vp, C.POINTER(_i32), C.POINTER(_i64), C.POINTER(_i64)]),
     "cmb3d_plan_schedule": (_i32, [_vp, C.POINTER(_i32)]),
+    "cmb3d_batch_schedule": (_i32, [_vp, C.POINTER(_i32), C.POINTER(_i32)]),
     "cmb3d_plan_set_schedule": (_i32, [_vp, C.POINTER(_i32)]),
     "cmb3d_destroy": (None, [_vp]),
     "cmb3d_strerror": (C.c_char_p, [_i32]),
@@ -212,6 +214,10 @@ def cmb3d_realize_sample_batch(plans, seeds, outs_dev, stream=None) -> None:
     _check(lib.cmb3d_realize_sample_batch(hp, hs, ho, B, _stream_ptr(stream)), "cmb3d_realize_sample_batch")
 
 
+def cmb3d_batch_debug(spin_limit: int = 0, withhold_draw: bool = False, force_form: int = -1) -> None:
+    load().cmb3d_batch_debug(int(spin_limit), int(bool(withhold_draw)), int(force_form))
+
+
 def cmb3d_draw_spectrum(plan: int, seed: int, spec_dev, stream=None) -> None:
     lib = load()
     _check(lib.cmb3d_draw_spectrum(plan, int(seed) & 0xFFFFFFFFFFFFFFFF, _dev_ptr(spec_dev), _stream_ptr(stream)),
@@ -265,6 +271,14 @@ def cmb3d_plan_schedule(plan: int) -> tuple[int, int, int, int]:
     out = (_i32 * 4)()
     _check(lib.cmb3d_plan_schedule(plan, out), "cmb3d_plan_schedule")
     return tuple(out)
+
+
+def cmb3d_batch_schedule(plan: int) -> tuple[int, int]:
+    """(form, variant) of the batched path last built with `plan` first."""
+    lib = load()
+    f, v = _i32(), _i32()
+    _check(lib.cmb3d_batch_schedule(plan, C.byref(f), C.byref(v)), "cmb3d_batch_schedule")
+    return f.value, v.value
 
 
 def cmb3d_plan_set_schedule(plan: int, sched) -> None:

@@ -1,0 +1,144 @@
+// Device bodies of the realization passes, shared by the per-pass kernels
+// (fft_passes.cu) and the persistent batch kernel (batch.cu).
+#pragma once
+
+#include "device_common.cuh"
+
+namespace cmb3d {
+
+
+// Fourier coefficients of the modes (mx, my, mz) and (mx, my, mz + N/2),
+// mz < N/2, which share the Philox counter (mx, my, mz, 0): words (0, 1) draw
+// the first, words (2, 3) the second.
+
+// On a Hermitian plane mx in {0, N/2}: the mode with the smaller index
+// mz N + my of a conjugate pair draws from its own counter and its partner
+// takes the conjugate; self-conjugate modes are real with variance P_box; the
+// DC mode is zero.  The partners of the two modes also share one counter.
+template <int N>
+__device__ __forceinline__ void draw_hermitian_pair(int mx, int my, int mz, const float* __restrict__ amp,
+                                                    uint2 key, float2& lo, float2& hi) {
+  constexpr int H = N / 2;
+  const int py = (N - my) & (N - 1);
+  const int pz_lo = (N - mz) & (N - 1), pz_hi = (pz_lo + H) & (N - 1);
+  const int fy = my <= H ? my : my - N;
+  const int q_lo = mx * mx + fy * fy + mz * mz;
+  const int fz_hi = mz + H <= H ? mz + H : mz + H - N;
+  const int q_hi = mx * mx + fy * fy + fz_hi * fz_hi;
+  const uint4 own = philox4x32_10(make_uint4(mx, my, mz, 0u), key);
+  const uint4 par = philox4x32_10(make_uint4(mx, py, pz_lo & (H - 1), 0u), key);
+  // partner words: the partner of mode lo is pz_lo (lo words if pz_lo < H)
+  const bool plo_is_lo = pz_lo < H;
+  float2 out[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int z = h ? mz + H : mz, pz = h ? pz_hi : pz_lo, q = h ? q_hi : q_lo;
+    const int lin = z * N + my, plin = pz * N + py;
+    const float a = __ldg(amp + q);
+    const float2 g_own = h ? box_muller(own.z, own.w) : box_muller(own.x, own.y);
+    if (lin == plin) {
+      out[h] = q == 0 ? make_float2(0.f, 0.f) : make_float2(a * 1.41421356237309505f * g_own.x, 0.f);
+    } else if (lin < plin) {
+      out[h] = make_float2(a * g_own.x, a * g_own.y);
+    } else {
+      const bool use_lo = (h == 0) == plo_is_lo;
+      const float2 g = use_lo ? box_muller(par.x, par.y) : box_muller(par.z, par.w);
+      out[h] = make_float2(a * g.x, -a * g.y);
+    }
+  }
+  lo = out[0];
+  hi = out[1];
+}
+
+// Entries (m_x', m_y, mz) and (m_x', m_y, mz + N/2) of the packed half spectrum.
+template <int N>
+__device__ __forceinline__ void draw_packed_pair(int xp, int my, int mz, const float* __restrict__ amp,
+                                                 uint2 key, float2& lo, float2& hi) {
+  constexpr int H = N / 2;
+  if (xp == 0) {
+    float2 A0, A1, B0, B1;
+    draw_hermitian_pair<N>(0, my, mz, amp, key, A0, A1);
+    draw_hermitian_pair<N>(H, my, mz, amp, key, B0, B1);
+    lo = make_float2(A0.x - B0.y, A0.y + B0.x);
+    hi = make_float2(A1.x - B1.y, A1.y + B1.x);
+    return;
+  }
+  const int fy = my <= H ? my : my - N;
+  const int fz_hi = mz + H <= H ? mz + H : mz + H - N;
+  const int base = xp * xp + fy * fy;
+  const float a_lo = __ldg(amp + base + mz * mz), a_hi = __ldg(amp + base + fz_hi * fz_hi);
+  const uint4 w = philox4x32_10(make_uint4(xp, my, mz, 0u), key);
+  const float2 g0 = box_muller(w.x, w.y), g1 = box_muller(w.z, w.w);
+  lo = make_float2(a_lo * g0.x, a_lo * g0.y);
+  hi = make_float2(a_hi * g1.x, a_hi * g1.y);
+}
+
+// Draw + inverse FFT along z of the T adjacent columns x0 .. x0+T-1 of row
+// m_y (blockDim.x == T * N / R): one thread draws the mode pairs
+// (m_z, m_z + N/2) of its column for its first-stage inputs.
+template <int N, int R, int T>
+__device__ __forceinline__ void draw_zfft_tile(float2* __restrict__ buf, const float* __restrict__ amp,
+                                               const float2* __restrict__ tw, uint2 key, int x0, int my,
+                                               float2* sm) {
+  constexpr int N2 = N / 2, NB = N / R;
+  const int c = threadIdx.x % T, j = threadIdx.x / T;
+  const int xp = x0 + c;
+  float2 v[R];
+#pragma unroll
+  for (int r = 0; r < R / 2; ++r) draw_packed_pair<N>(xp, my, j + r * NB, amp, key, v[r], v[r + R / 2]);
+  float2* col = buf + static_cast<size_t>(my) * N2 + xp;   // (z, my, xp) at col[z N N2]
+  stockham<N, R, N, false>(
+      v, sm, tw, j, [&](int n) { return n * T + c; },
+      [&](int n, float2 x) { col[static_cast<size_t>(n) * N * N2] = x; }, BlockSync{});
+}
+
+// In-place inverse FFT along y of the T adjacent columns x0 .. x0+T-1 of one
+// z-plane (plane points at element (z, 0, 0)); blockDim.x == T * N / R.
+// Loads and stores go through L2 only (.cg), so the data may have been written
+// by other thread blocks of the same cluster.
+template <int N, int R, int T>
+__device__ __forceinline__ void yfft_tile(float2* __restrict__ plane, int x0, float2* sm,
+                                          const float2* __restrict__ tw) {
+  constexpr int N2 = N / 2, NB = N / R;
+  const int c = threadIdx.x % T, j = threadIdx.x / T;
+  float2* col = plane + x0 + c;                                   // (y, x0 + c) at col[y N2]
+  float2 v[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) v[r] = __ldcg(col + static_cast<size_t>(j + r * NB) * N2);
+  stockham<N, R, N, false>(
+      v, sm, tw, j, [&](int n) { return n * T + c; },
+      [&](int n, float2 x) { __stcg(col + static_cast<size_t>(n) * N2, x); }, BlockSync{});
+}
+
+// Row pass: for k in [0, N/2) the half-length input is
+//   Y[k] = (G[k] + conj(G[N/2-k])) + i w^k (G[k] - conj(G[N/2-k])),  w = e^{2 pi i/N},
+// with G[0], G[N/2] the real and imaginary parts of the packed entry 0, so that
+// the N/2-point inverse FFT y[n] = f(2n) + i f(2n+1) is the real row itself.
+template <int N, int R, int ROWS>
+__device__ __forceinline__ void xc2r_rows(float2* __restrict__ rows, float2* sm, const float2* __restrict__ tw) {
+  constexpr int N2 = N / 2, NB = N2 / R;
+  constexpr int P = N2 + (N2 >> 4);            // row pitch: one pad slot per 16 entries
+  const int j = threadIdx.x % NB, rl = threadIdx.x / NB;
+  float2* g = rows + static_cast<size_t>(rl) * N2;
+  auto sidx = [&](int n) { return rl * P + n + (n >> 4); };
+  float2 v[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) v[r] = __ldcg(g + j + r * NB);     // all loads in flight at once
+#pragma unroll
+  for (int r = 0; r < R; ++r) sm[sidx(j + r * NB)] = v[r];
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int k = j + r * NB;
+    if (k == 0) {
+      const float2 p = sm[sidx(0)];
+      v[r] = make_float2(p.x + p.y, p.x - p.y);
+    } else {
+      const float2 a = sm[sidx(k)], b = cconj(sm[sidx(N2 - k)]);
+      v[r] = cadd(cadd(a, b), cmul_i(cmul(__ldg(tw + k), csub(a, b))));
+    }
+  }
+  stockham<N2, R, N, true>(v, sm, tw, j, sidx, [&](int n, float2 x) { g[n] = x; }, BlockSync{});
+}
+
+}  // namespace cmb3d

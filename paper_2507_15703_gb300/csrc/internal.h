@@ -18,8 +18,9 @@ int num_col_variants(int N);
 int num_row_variants(int N);
 int num_fused_variants(int N);
 
+// key_dev != NULL: read the Philox key (seed lo, seed hi) from device memory.
 cudaError_t launch_draw_zfft(int N, int v, float2* buf, const float* amp, const float2* tw,
-                             uint64_t seed, cudaStream_t s);
+                             uint64_t seed, cudaStream_t s, const uint2* key_dev = nullptr);
 
 // Diagnostic: the drawn packed half spectrum [m_z][m_y][m_x'], untransformed.
 cudaError_t launch_draw_only(int N, float2* buf, const float* amp, uint64_t seed, cudaStream_t s);
@@ -39,6 +40,32 @@ cudaError_t launch_xc2r(int N, int v, float2* buf, const float2* tw, cudaStream_
 // be NULL for the identity).
 cudaError_t launch_gather(int N, int interp, const float* field, const float4* tab,
                           const int32_t* perm, float* out, int64_t npix, cudaStream_t s);
+
+// ---- persistent batch kernel (batch.cu) ----------------------------------
+struct BatchBox {
+  float2* buf;            // the box's packed spectrum / field
+  const float* amp;       // its amplitude table
+  const float4* tab;      // its pixel table (gather order)
+  const int32_t* perm;    // gather order -> caller order, or NULL
+  float* out;             // caller's output
+  int npix;
+  uint32_t key_lo, key_hi;
+};
+enum { kBatchDraw = 0, kBatchY = 1, kBatchX = 2, kBatchG = 3 };
+constexpr int kBatchTilesPerItem = 4;
+constexpr int kBatchPixelsPerItem = 4096;
+// Work item: box << 40 | type << 32 | index within (box, type).
+inline uint64_t batch_item(int box, int type, int idx) {
+  return (static_cast<uint64_t>(box) << 40) | (static_cast<uint64_t>(type) << 32) | static_cast<uint32_t>(idx);
+}
+bool batch_supported(int N);
+void batch_item_counts(int N, int* nD, int* nY, int* nX);
+int num_batch_variants();
+cudaError_t batch_grid(int N, int interp, int v, int* blocks);
+// ctr: [0] next item, [1] error word, [2 + 4 b + type] items of (b, type) done.
+cudaError_t launch_batch(int N, int interp, int v, int grid, const BatchBox* boxes, const uint64_t* items,
+                         int nitems, unsigned* ctr, const float2* tw, unsigned spin_limit, int withhold,
+                         cudaStream_t s);
 
 // Philox4x32-10 words of n counters (uint4 each).
 cudaError_t launch_philox(const uint32_t* ctr, uint64_t seed, uint32_t* out, int64_t n,

@@ -45,6 +45,49 @@ struct Schedule {
   int draw = 0, y = 0, x = 0, fused = -1;
 };
 
+// State of the persistent batch path, kept in the first plan of a batch: the
+// device work list and descriptors of the last plan set, and the CUDA graph
+// (counter reset + persistent launch) captured for it.
+// Forms: kBatchPersistent (variant = blocks-per-SM variant of the persistent
+// kernel) or kBatchStreams (a graph of two streams: the draws of all boxes on
+// one, each box's y, x and gather passes on a higher-priority one gated by its
+// draw, so draws overlap earlier boxes' memory-bound passes).
+enum { kBatchPersistent = 0, kBatchStreams = 1 };
+
+struct BatchCtx {
+  std::vector<const void*> plans;
+  unsigned spin_limit = 0;
+  int withhold = 0;
+  int form = -1;
+  int variant = 0;
+  int grid = 0, nitems = 0;
+  cmb3d::BatchBox* d_boxes = nullptr;
+  uint64_t* d_items = nullptr;
+  unsigned* d_ctr = nullptr;
+  uint2* d_keys = nullptr;
+  size_t ctr_words = 0;
+  std::vector<cmb3d::BatchBox> h_boxes;
+  std::vector<uint2> h_keys;
+  cudaStream_t cap = nullptr, cap2 = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  void release() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (cap) cudaStreamDestroy(cap);
+    if (cap2) cudaStreamDestroy(cap2);
+    cudaFree(d_boxes);
+    cudaFree(d_items);
+    cudaFree(d_ctr);
+    cudaFree(d_keys);
+    *this = BatchCtx();
+  }
+};
+
+unsigned g_batch_spin_limit = 1u << 22;   // polls of a bounded wait (about 2 s)
+int g_batch_withhold = 0;                 // fault injection: D items never report done
+int g_batch_force = -1;                   // tests: 0, 1 persistent variant; 2 two-stream graph
+
 }  // namespace
 
 struct cmb3d_plan_s {
@@ -67,6 +110,9 @@ struct cmb3d_plan_s {
   size_t tnext = 0;
   Schedule sched;
   bool tuned = false;
+  BatchCtx batch;
+  std::vector<const void*> batch_tuned_sig;   // plan set + outputs the batch autotune ran on
+  int batch_best_form = 0, batch_best_v = 0;
 };
 
 namespace {
@@ -100,6 +146,7 @@ int dev_alloc(cmb3d_plan_s* p, T** ptr, size_t count, const char* what) {
 void free_plan(cmb3d_plan_s* p) {
   if (!p) return;
   DeviceGuard g(p->device);
+  p->batch.release();
   cudaFree(p->buf);
   cudaFree(p->amp);
   cudaFree(p->tw);
@@ -505,21 +552,254 @@ int cmb3d_realize_sample_to_host(cmb3d_plan_t p, uint64_t seed, float* out_host,
   return CMB3D_OK;
 }
 
+namespace {
+
+// Work list of a batch: round t lists the draw items of box t interleaved, by
+// proportional position, with the y, x and gather items of box t-kLag, so the
+// draws a pass waits for were handed out a full round earlier.
+std::vector<uint64_t> batch_work_list(const cmb3d_plan_t* plans, int B, int N) {
+  int nD, nY, nX;
+  cmb3d::batch_item_counts(N, &nD, &nY, &nX);
+  constexpr int kLag = 2;
+  std::vector<uint64_t> items;
+  for (int t = 0; t < B + kLag; ++t) {
+    std::vector<uint64_t> a, b;
+    if (t < B)
+      for (int i = 0; i < nD; ++i) a.push_back(cmb3d::batch_item(t, cmb3d::kBatchDraw, i));
+    if (t >= kLag) {
+      const int bx = t - kLag;
+      const int nG = static_cast<int>((plans[bx]->npix + cmb3d::kBatchPixelsPerItem - 1) / cmb3d::kBatchPixelsPerItem);
+      for (int i = 0; i < nY; ++i) b.push_back(cmb3d::batch_item(bx, cmb3d::kBatchY, i));
+      for (int i = 0; i < nX; ++i) b.push_back(cmb3d::batch_item(bx, cmb3d::kBatchX, i));
+      for (int i = 0; i < nG; ++i) b.push_back(cmb3d::batch_item(bx, cmb3d::kBatchG, i));
+    }
+    size_t i = 0, j = 0;
+    while (i < a.size() || j < b.size()) {
+      const double ka = i < a.size() ? (i + 0.5) / a.size() : 2.0;
+      const double kb = j < b.size() ? (j + 0.5) / b.size() : 2.0;
+      items.push_back(ka <= kb ? a[i++] : b[j++]);
+    }
+  }
+  return items;
+}
+
+int batch_persistent(const cmb3d_plan_t* plans, const uint64_t* seeds, float* const* outs, int B, cudaStream_t s,
+                     int variant);
+int batch_streams(const cmb3d_plan_t* plans, const uint64_t* seeds, float* const* outs, int B, cudaStream_t s);
+
+int batch_form(const cmb3d_plan_t* plans, const uint64_t* seeds, float* const* outs, int B, cudaStream_t s, int form,
+               int variant) {
+  return form == kBatchStreams ? batch_streams(plans, seeds, outs, B, s)
+                               : batch_persistent(plans, seeds, outs, B, s, variant);
+}
+
+// Form to use: the persistent kernel by default; with CMB3D_FLAG_AUTOTUNE on
+// plans[0], each persistent variant and the two-stream graph are timed once
+// on this plan set (build, then one timed run) and the fastest is kept.
+int batch_run(const cmb3d_plan_t* plans, const uint64_t* seeds, float* const* outs, int B, cudaStream_t s) {
+  cmb3d_plan_s* lead = plans[0];
+  if (g_batch_force >= 0)
+    return g_batch_force >= cmb3d::num_batch_variants() ? batch_streams(plans, seeds, outs, B, s)
+                                                         : batch_persistent(plans, seeds, outs, B, s, g_batch_force);
+  if (!(lead->flags & CMB3D_FLAG_AUTOTUNE)) return batch_persistent(plans, seeds, outs, B, s, 0);
+  std::vector<const void*> sig(plans, plans + B);
+  sig.insert(sig.end(), outs, outs + B);
+  if (lead->batch_tuned_sig == sig) return batch_form(plans, seeds, outs, B, s, lead->batch_best_form, lead->batch_best_v);
+  float best = 1e30f;
+  int best_form = kBatchPersistent, best_v = 0;
+  std::vector<std::pair<int, int>> cands;
+  for (int v = 0; v < cmb3d::num_batch_variants(); ++v) cands.emplace_back(kBatchPersistent, v);
+  cands.emplace_back(kBatchStreams, 0);
+  for (const auto& c : cands) {
+    int st = batch_form(plans, seeds, outs, B, s, c.first, c.second);    // builds the form
+    if (st != CMB3D_OK) return st;
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return fail_cuda(cudaErrorUnknown, "batch autotune event");
+    if (cudaEventCreate(&b) != cudaSuccess) {
+      cudaEventDestroy(a);
+      return fail_cuda(cudaErrorUnknown, "batch autotune event");
+    }
+    cudaEventRecord(a, s);
+    st = batch_form(plans, seeds, outs, B, s, c.first, c.second);
+    cudaEventRecord(b, s);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (st != CMB3D_OK) return st;
+    if (ms < best) best = ms, best_form = c.first, best_v = c.second;
+  }
+  lead->batch_tuned_sig = sig;
+  lead->batch_best_form = best_form;
+  lead->batch_best_v = best_v;
+  return batch_form(plans, seeds, outs, B, s, best_form, best_v);
+}
+
+int batch_streams(const cmb3d_plan_t* plans, const uint64_t* seeds, float* const* outs, int B, cudaStream_t s) {
+  cmb3d_plan_s* lead = plans[0];
+  BatchCtx& bc = lead->batch;
+  const int N = lead->N;
+  std::vector<const void*> sig(plans, plans + B);
+  sig.insert(sig.end(), outs, outs + B);
+  cudaError_t e = cudaSuccess;
+  if (bc.form != kBatchStreams || bc.plans != sig) {
+    bc.release();
+    bc.form = kBatchStreams;
+    bc.plans = sig;
+    for (int b = 0; b < B; ++b)
+      if ((plans[b]->flags & CMB3D_FLAG_AUTOTUNE) && !plans[b]->tuned) {
+        int st = autotune(plans[b], s);
+        if (st != CMB3D_OK) return st;
+      }
+    int lo = 0, hi = 0;
+    std::vector<cudaEvent_t> ev(static_cast<size_t>(B) + 2, nullptr);
+    bool ok = cudaDeviceGetStreamPriorityRange(&lo, &hi) == cudaSuccess &&
+              cudaMalloc(reinterpret_cast<void**>(&bc.d_keys), sizeof(uint2) * B) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&bc.cap, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithPriority(&bc.cap2, cudaStreamNonBlocking, hi) == cudaSuccess;
+    for (auto& x : ev) ok = ok && cudaEventCreateWithFlags(&x, cudaEventDisableTiming) == cudaSuccess;
+    if (ok && (e = cudaStreamBeginCapture(bc.cap, cudaStreamCaptureModeThreadLocal)) == cudaSuccess) {
+      cudaError_t el = cudaEventRecord(ev[static_cast<size_t>(B)], bc.cap);
+      if (el == cudaSuccess) el = cudaStreamWaitEvent(bc.cap2, ev[static_cast<size_t>(B)], 0);
+      for (int b = 0; b < B && el == cudaSuccess; ++b) {
+        cmb3d_plan_s* p = plans[b];
+        const Schedule& sc = p->sched;
+        el = cmb3d::launch_draw_zfft(N, sc.draw, p->buf, p->amp, p->tw, 0, bc.cap, bc.d_keys + b);
+        if (el == cudaSuccess) el = cudaEventRecord(ev[static_cast<size_t>(b)], bc.cap);
+        if (el == cudaSuccess) el = cudaStreamWaitEvent(bc.cap2, ev[static_cast<size_t>(b)], 0);
+        if (el == cudaSuccess) {
+          if (sc.fused >= 0) {
+            el = cmb3d::launch_yx_fused(N, sc.fused, p->buf, p->tw, bc.cap2);
+          } else {
+            el = cmb3d::launch_yfft(N, sc.y, p->buf, p->tw, bc.cap2);
+            if (el == cudaSuccess) el = cmb3d::launch_xc2r(N, sc.x, p->buf, p->tw, bc.cap2);
+          }
+        }
+        if (el == cudaSuccess)
+          el = cmb3d::launch_gather(N, p->interp, reinterpret_cast<const float*>(p->buf), p->tab, p->perm, outs[b],
+                                    p->npix, bc.cap2);
+      }
+      if (el == cudaSuccess) el = cudaEventRecord(ev[static_cast<size_t>(B) + 1], bc.cap2);
+      if (el == cudaSuccess) el = cudaStreamWaitEvent(bc.cap, ev[static_cast<size_t>(B) + 1], 0);
+      e = cudaStreamEndCapture(bc.cap, &bc.graph);
+      if (e == cudaSuccess) e = el;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&bc.exec, bc.graph, 0);
+    } else if (!ok) {
+      e = cudaErrorMemoryAllocation;
+    }
+    for (auto& x : ev)
+      if (x) cudaEventDestroy(x);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      bc.release();
+      return fail_cuda(e, "batch stream-graph capture");
+    }
+    bc.h_keys.resize(static_cast<size_t>(B));
+  }
+  for (int b = 0; b < B; ++b)
+    bc.h_keys[static_cast<size_t>(b)] = make_uint2(static_cast<uint32_t>(seeds[b] & 0xFFFFFFFFu),
+                                                   static_cast<uint32_t>(seeds[b] >> 32));
+  if ((e = cudaMemcpyAsync(bc.d_keys, bc.h_keys.data(), sizeof(uint2) * B, cudaMemcpyHostToDevice, s)) !=
+          cudaSuccess ||
+      (e = cudaGraphLaunch(bc.exec, s)) != cudaSuccess || (e = cudaStreamSynchronize(s)) != cudaSuccess)
+    return fail_cuda(e, "batch stream-graph launch");
+  return CMB3D_OK;
+}
+
+int batch_persistent(const cmb3d_plan_t* plans, const uint64_t* seeds, float* const* outs, int B, cudaStream_t s,
+                     int variant) {
+  cmb3d_plan_s* lead = plans[0];
+  BatchCtx& bc = lead->batch;
+  const int N = lead->N;
+  std::vector<const void*> sig(plans, plans + B);
+  cudaError_t e;
+  if (bc.form != kBatchPersistent || bc.plans != sig || bc.spin_limit != g_batch_spin_limit ||
+      bc.withhold != g_batch_withhold || bc.variant != variant) {
+    bc.release();
+    bc.form = kBatchPersistent;
+    bc.variant = variant;
+    std::vector<uint64_t> items = batch_work_list(plans, B, N);
+    bc.plans = sig;
+    bc.spin_limit = g_batch_spin_limit;
+    bc.withhold = g_batch_withhold;
+    bc.nitems = static_cast<int>(items.size());
+    bc.ctr_words = 2 + 4 * static_cast<size_t>(B);
+    if ((e = cmb3d::batch_grid(N, lead->interp, variant, &bc.grid)) != cudaSuccess ||
+        (e = cudaMalloc(reinterpret_cast<void**>(&bc.d_boxes), sizeof(cmb3d::BatchBox) * B)) != cudaSuccess ||
+        (e = cudaMalloc(reinterpret_cast<void**>(&bc.d_items), sizeof(uint64_t) * items.size())) != cudaSuccess ||
+        (e = cudaMalloc(reinterpret_cast<void**>(&bc.d_ctr), sizeof(unsigned) * bc.ctr_words)) != cudaSuccess ||
+        (e = cudaMemcpy(bc.d_items, items.data(), sizeof(uint64_t) * items.size(), cudaMemcpyHostToDevice)) !=
+            cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&bc.cap, cudaStreamNonBlocking)) != cudaSuccess) {
+      bc.release();
+      return fail_cuda(e, "batch set-up");
+    }
+    // capture: reset the counters, run the persistent kernel
+    if ((e = cudaStreamBeginCapture(bc.cap, cudaStreamCaptureModeThreadLocal)) == cudaSuccess) {
+      cudaError_t e1 = cudaMemsetAsync(bc.d_ctr, 0, sizeof(unsigned) * bc.ctr_words, bc.cap);
+      cudaError_t e2 = cmb3d::launch_batch(N, lead->interp, variant, bc.grid, bc.d_boxes, bc.d_items, bc.nitems,
+                                           bc.d_ctr, lead->tw, bc.spin_limit, bc.withhold, bc.cap);
+      e = cudaStreamEndCapture(bc.cap, &bc.graph);
+      if (e == cudaSuccess) e = e1 != cudaSuccess ? e1 : e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&bc.exec, bc.graph, 0);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      bc.release();
+      return fail_cuda(e, "batch graph capture");
+    }
+    bc.h_boxes.resize(static_cast<size_t>(B));
+  }
+  for (int b = 0; b < B; ++b) {
+    const cmb3d_plan_s* p = plans[b];
+    bc.h_boxes[static_cast<size_t>(b)] = cmb3d::BatchBox{p->buf,  p->amp, p->tab, p->perm, outs[b], static_cast<int>(p->npix),
+                                                        static_cast<uint32_t>(seeds[b] & 0xFFFFFFFFu),
+                                                        static_cast<uint32_t>(seeds[b] >> 32)};
+  }
+  // descriptors from pageable memory: the call returns once they are staged
+  if ((e = cudaMemcpyAsync(bc.d_boxes, bc.h_boxes.data(), sizeof(cmb3d::BatchBox) * B, cudaMemcpyHostToDevice, s)) !=
+          cudaSuccess ||
+      (e = cudaGraphLaunch(bc.exec, s)) != cudaSuccess)
+    return fail_cuda(e, "batch launch");
+  unsigned h_err = 0;
+  if ((e = cudaMemcpyAsync(&h_err, bc.d_ctr + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess)
+    return fail_cuda(e, "batch completion");
+  if (h_err) return fail(CMB3D_ETIMEOUT, "a bounded wait in the persistent batch kernel gave up");
+  return CMB3D_OK;
+}
+
+}  // namespace
+
 int cmb3d_realize_sample_batch(const cmb3d_plan_t* plans, const uint64_t* seeds, float* const* outs_dev, int B,
                                void* stream) {
   if (B < 0 || (B > 0 && (!plans || !seeds || !outs_dev))) return fail(CMB3D_EINVAL, "bad batch arrays");
+  if (B == 0) return CMB3D_OK;
   for (int b = 0; b < B; ++b) {
     int st = check_ready(plans[b]);
     if (st != CMB3D_OK) return st;
-    if (plans[b]->N != plans[0]->N || plans[b]->L != plans[0]->L || plans[b]->interp != plans[0]->interp)
-      return fail(CMB3D_EINVAL, "batched plans must share N, L and interp");
+    if (plans[b]->N != plans[0]->N || plans[b]->L != plans[0]->L || plans[b]->interp != plans[0]->interp ||
+        plans[b]->device != plans[0]->device)
+      return fail(CMB3D_EINVAL, "batched plans must share N, L, interp and device");
     if (plans[b]->npix > 0 && !outs_dev[b]) return fail(CMB3D_EINVAL, "outs_dev entry is NULL");
+    for (int c = 0; c < b; ++c)
+      if (plans[c] == plans[b]) return fail(CMB3D_EINVAL, "a plan appears twice in the batch (one box buffer each)");
   }
+  DeviceGuard g(plans[0]->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cmb3d::batch_supported(plans[0]->N)) return batch_run(plans, seeds, outs_dev, B, s);
   for (int b = 0; b < B; ++b) {
     int st = cmb3d_realize_sample(plans[b], seeds[b], outs_dev[b], stream);
     if (st != CMB3D_OK) return st;
   }
   return CMB3D_OK;
+}
+
+void cmb3d_batch_debug(uint32_t spin_limit, int withhold_draw, int force_form) {
+  g_batch_spin_limit = spin_limit ? spin_limit : (1u << 22);
+  g_batch_withhold = withhold_draw ? 1 : 0;
+  g_batch_force = force_form >= 0 && force_form <= cmb3d::num_batch_variants() ? force_form : -1;
 }
 
 int cmb3d_draw_spectrum(cmb3d_plan_t p, uint64_t seed, void* spec_dev, void* stream) {
@@ -610,6 +890,13 @@ int cmb3d_plan_set_schedule(cmb3d_plan_t p, const int* sched) {
   }
   p->sched = sc;
   p->tuned = true;
+  return CMB3D_OK;
+}
+
+int cmb3d_batch_schedule(cmb3d_plan_t p, int* form, int* variant) {
+  if (!p || !form || !variant) return fail(CMB3D_EINVAL, "NULL argument");
+  *form = p->batch.form;
+  *variant = p->batch.variant;
   return CMB3D_OK;
 }
 

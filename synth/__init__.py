@@ -100,6 +100,8 @@ class Workload:
     L_over_r: float = 2.2   # box side in units of r
     amplitude: float = 1e3
     period: float = 22.0
+    batch: int = 1          # boxes per step; > 1: each box has its own cap
+    fsky_seed: int = 2507   # seed of the per-box sky fractions (batch > 1)
 
     @property
     def L(self) -> float:
@@ -107,6 +109,10 @@ class Workload:
 
     def pixels(self) -> np.ndarray:
         return cap_pixels(self.nside, self.fsky)
+
+    def batch_pixels(self) -> list[np.ndarray]:
+        """Per-box pixel sets: caps with f_sky uniform on [0.05, 0.5]."""
+        return [cap_pixels(self.nside, float(f)) for f in batch_fsky(self.batch, self.fsky_seed)]
 
     def cl(self) -> tuple[np.ndarray, np.ndarray]:
         return cl_family(self.lmax, self.amplitude, self.period, self.damping)
@@ -119,6 +125,10 @@ WORKLOADS = {
     # 512^3 box, ~5M cap pixels, tricubic: the single-realization production workload.
     "box512_cap0.4_tricubic": Workload("box512_cap0.4_tricubic", N=512, nside=1024, fsky=0.4,
                                        lmax=768, damping=600.0, interp=3),
+    # 64 boxes of 256^3 per step, each with its own cap (f_sky ~ U[0.05, 0.5]
+    # of a 12*512^2-point grid, ~55M pixels in all), trilinear.
+    "batch64_box256_trilinear": Workload("batch64_box256_trilinear", N=256, nside=512, fsky=0.275,
+                                         lmax=128, damping=100.0, interp=1, batch=64),
     # 1024^3 box, ~20M cap pixels, tricubic.
     "box1024_cap0.4_tricubic": Workload("box1024_cap0.4_tricubic", N=1024, nside=2048, fsky=0.4,
                                         lmax=768, damping=600.0, interp=3),
