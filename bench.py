@@ -187,6 +187,8 @@ def run_cuda(args, rank, world, local):
         flags |= cmb3d.CMB3D_FLAG_THREE_PASS
     if args.fused:
         flags |= cmb3d.CMB3D_FLAG_FUSED_YX
+    if args.fp16_gemm:
+        flags |= cmb3d.CMB3D_FLAG_FP16_GEMM
     plan = cmb3d.Plan(w.N, w.L, w.r, pix, w.interp, flags)
     fit_err = plan.set_cl(ell, cl, w.nkbins)
     setup_s = time.time() - t0
@@ -257,7 +259,8 @@ def run_cuda(args, rank, world, local):
               "interp": "tricubic" if w.interp == 3 else "trilinear", "lmax": w.lmax, "nkbins": w.nkbins,
               "parallelism": f"replicas x{world}",
               "schedule": {"draw": schedule[0], "y": schedule[1], "x": schedule[2], "fused_yx": schedule[3],
-                           "restriction": "three-pass" if args.three_pass else "fused" if args.fused else "autotuned"},
+                           "restriction": "three-pass" if args.three_pass else "fused" if args.fused else "autotuned",
+                           "y_pass": "split-FP16 DFT-GEMM (tcgen05)" if args.fp16_gemm else "FP32 butterflies"},
               "l2": f"no flush: per-map working set {per_map_bytes / 2**30:.2f} GiB > 129 MiB L2",
               "cl_fit_max_rel_err": fit_err, "plan_setup_s": round(setup_s, 2)}
     emit(args, w, value, t_max, world, config, per_map_bytes, kernels, dom, maps / e2e_s, 4 * npix,
@@ -407,7 +410,7 @@ def emit(args, w, value, t_max, world, config, per_map_bytes, kernels, dom, e2e_
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32",
+        "dtype": "f32" if not getattr(args, "fp16_gemm", False) else "f32 (y pass: f16 hi+lo GEMM, f32 accumulate)",
         "data": "synthetic: Fibonacci-grid polar cap pixels, C_l family inverted to P(k) by the library's NNLS",
         "config": config,
         "achieved_gbs_alg_per_map": round(per_map_bytes * value / world / 1e9, 1),
@@ -517,6 +520,8 @@ def main():
     ap.add_argument("--three-pass", action="store_true", help="only separate y and x passes")
     ap.add_argument("--fused", action="store_true", help="only the fused y+x pass")
     ap.add_argument("--sweep", action="store_true", help="also time every kernel variant (stderr)")
+    ap.add_argument("--fp16-gemm", action="store_true",
+                    help="y pass with split-FP16 DFT-GEMM stages on the tensor cores")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":

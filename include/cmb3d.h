@@ -70,9 +70,13 @@ enum {
   CMB3D_FLAG_THREE_PASS = 1u << 3,    /* only separate y and x passes                  */
   CMB3D_FLAG_FUSED_YX = 1u << 4,      /* the fused y+x pass where it exists
                                          (128 <= N <= 1024)                            */
-  CMB3D_FLAG_AUTOTUNE = 1u << 5       /* at the first realization, time every kernel
+  CMB3D_FLAG_AUTOTUNE = 1u << 5,      /* at the first realization, time every kernel
                                          shape of this N and keep the fastest (cached
                                          per device and N for the process)            */
+  CMB3D_FLAG_FP16_GEMM = 1u << 6      /* y pass with its radix-16 stages as split-FP16
+                                         (hi+lo) DFT-GEMMs on the tensor cores, FP32
+                                         accumulation (N = 256, 512, 1024; else
+                                         CMB3D_EUNSUPPORTED); tolerance 1e-3 of rms    */
 };
 
 /* Spectrum kinds for cmb3d_set_spectrum. */
@@ -172,7 +176,8 @@ int cmb3d_realize_sample(cmb3d_plan_t plan, uint64_t seed, float* out_dev, void*
 /*
  * The same map delivered to host memory: enqueues cmb3d_realize_sample into the
  * plan's staging buffer, copies the npix floats to out_host (pinned memory is
- * fastest) and synchronises the stream before returning.
+ * fastest) and synchronises the stream before returning.  CMB3D_ETIMEOUT if a
+ * bounded device-side wait gave up (tensor-core stage).
  */
 int cmb3d_realize_sample_to_host(cmb3d_plan_t plan, uint64_t seed, float* out_host,
                                  void* stream);
@@ -238,7 +243,9 @@ int cmb3d_philox4x32_10(const uint32_t* ctr_dev, uint64_t seed, uint32_t* out_de
  * plans made with CMB3D_FLAG_STAGE_TIMING (CMB3D_EINVAL otherwise).  ms[0..n)
  * receives stages CMB3D_STAGE_*; launches[0..n) (may be NULL) the number of
  * kernel launches timed per stage.  Synchronises on the recorded events.
- * reset != 0 clears the accumulators after reading.
+ * reset != 0 clears the accumulators after reading.  Returns CMB3D_ETIMEOUT
+ * (once) if a bounded device-side wait of the plan's kernels gave up since
+ * the last check.
  */
 int cmb3d_stage_times(cmb3d_plan_t plan, double* ms, int64_t* launches, int n, int reset);
 

@@ -33,6 +33,7 @@ CMB3D_FLAG_STAGE_TIMING = 1 << 2
 CMB3D_FLAG_THREE_PASS = 1 << 3
 CMB3D_FLAG_FUSED_YX = 1 << 4
 CMB3D_FLAG_AUTOTUNE = 1 << 5
+CMB3D_FLAG_FP16_GEMM = 1 << 6
 
 CMB3D_SPEC_PK = 0
 CMB3D_SPEC_CL = 1

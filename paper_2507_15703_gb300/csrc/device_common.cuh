@@ -160,9 +160,18 @@ __device__ __forceinline__ float2 box_muller(uint32_t w0, uint32_t w1) {
 //   sync  functor providing the barrier among the threads sharing the tile.
 // If FIRST_SYNC, a barrier precedes the first shared-memory write (needed when
 // the first-stage inputs were read from the same shared buffer).
-template <int NF, int R, int TWN, bool FIRST_SYNC, class SIdx, class Out, class Sync>
+struct RegisterDft {
+  template <int R>
+  __device__ __forceinline__ void operator()(float2 (&v)[R]) const {
+    IDft<R>::run(v);
+  }
+};
+
+// `dft` performs the radix-R transforms of the full stages (all threads call
+// it together); the default does them in registers.
+template <int NF, int R, int TWN, bool FIRST_SYNC, class SIdx, class Out, class Sync, class Dft = RegisterDft>
 __device__ __forceinline__ void stockham(float2 (&v)[R], float2* sm, const float2* __restrict__ tw,
-                                         int j, SIdx sidx, Out out, Sync sync) {
+                                         int j, SIdx sidx, Out out, Sync sync, Dft dft = Dft()) {
   constexpr int LR = ilog2c(R), LN = ilog2c(NF);
   constexpr int S = LN / LR;                       // full radix-R stages
   constexpr int R2 = 1 << (LN - S * LR);           // remainder radix (1 = none)
@@ -183,7 +192,7 @@ __device__ __forceinline__ void stockham(float2 (&v)[R], float2* sm, const float
 #pragma unroll
       for (int r = 1; r < R; ++r) v[r] = cmul(v[r], __ldg(tw + r * step));
     }
-    IDft<R>::run(v);
+    dft(v);
     if (R2 == 1 && s == S - 1) {
 #pragma unroll
       for (int r = 0; r < R; ++r) out(j + r * NB, v[r]);

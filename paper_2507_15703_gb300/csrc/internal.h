@@ -32,6 +32,11 @@ cudaError_t launch_yfft(int N, int v, float2* buf, const float2* tw, cudaStream_
 // L2 between the two axes); num_fused_variants(N) > 0 for 128 <= N <= 1024.
 cudaError_t launch_yx_fused(int N, int v, float2* buf, const float2* tw, cudaStream_t s);
 
+// FFT along y with the radix-16 stages as split-FP16 DFT-GEMMs on the tensor
+// cores (N = 256, 512, 1024).  *err is set if an MMA-completion wait gave up.
+bool yfft_gemm_supported(int N);
+cudaError_t launch_yfft_gemm(int N, float2* buf, const float2* tw, unsigned* err, cudaStream_t s);
+
 // Complex-to-real inverse FFT of every (z, y) row along x, in place.
 cudaError_t launch_xc2r(int N, int v, float2* buf, const float2* tw, cudaStream_t s);
 

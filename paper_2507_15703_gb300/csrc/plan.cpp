@@ -103,6 +103,7 @@ struct cmb3d_plan_s {
   float4* tab = nullptr;          // pixel table in gather order
   int32_t* perm = nullptr;        // gather order -> caller order (NULL = identity)
   float* outbuf = nullptr;        // staging for cmb3d_realize_sample_to_host
+  unsigned* d_err = nullptr;      // set by a kernel whose bounded wait gave up
   int64_t dev_bytes = 0;
   bool has_spec = false;
   std::vector<double> knodes, pnodes;
@@ -153,6 +154,7 @@ void free_plan(cmb3d_plan_s* p) {
   cudaFree(p->tab);
   cudaFree(p->perm);
   cudaFree(p->outbuf);
+  cudaFree(p->d_err);
   for (auto& r : p->recs) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -161,6 +163,28 @@ void free_plan(cmb3d_plan_s* p) {
 }
 
 bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+// y-pass variants: the butterfly shapes, then (where it exists) the
+// tensor-core split-FP16 form.
+int num_y_variants(int N) { return cmb3d::num_col_variants(N) + (cmb3d::yfft_gemm_supported(N) ? 1 : 0); }
+int gemm_y_variant(int N) { return cmb3d::yfft_gemm_supported(N) ? cmb3d::num_col_variants(N) : -1; }
+
+cudaError_t launch_y(cmb3d_plan_s* p, int v, cudaStream_t s) {
+  if (v == gemm_y_variant(p->N)) return cmb3d::launch_yfft_gemm(p->N, p->buf, p->tw, p->d_err, s);
+  return cmb3d::launch_yfft(p->N, v, p->buf, p->tw, s);
+}
+
+// Error word of the plan's kernels (synchronises); CMB3D_ETIMEOUT if set.
+int check_device_error(cmb3d_plan_s* p) {
+  unsigned h = 0;
+  cudaError_t e = cudaMemcpy(&h, p->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return fail_cuda(e, "error word read");
+  if (h) {
+    cudaMemset(p->d_err, 0, sizeof(unsigned));
+    return fail(CMB3D_ETIMEOUT, "a bounded wait for tensor-core MMA completion gave up");
+  }
+  return CMB3D_OK;
+}
 
 // Launch `f` on stream s, bracketed by CUDA events when the plan times stages.
 template <class F>
@@ -239,7 +263,7 @@ int autotune(cmb3d_plan_s* p, cudaStream_t s) {
     if (t < t_best) t_best = t, best.draw = v;
   }
   float t_y = 1e30f, t_x = 1e30f, t_f = 1e30f;
-  for (int v = 0; v < cmb3d::num_col_variants(N); ++v) {
+  for (int v = 0; v < cmb3d::num_col_variants(N); ++v) {   // butterfly forms only: FP16 is opt-in
     const float t = time_launches(s, [&] { return cmb3d::launch_yfft(N, v, p->buf, p->tw, s); }, &ok);
     if (!ok) return fail_cuda(cudaErrorLaunchFailure, "autotune yfft");
     if (t < t_y) t_y = t, best.y = v;
@@ -256,6 +280,7 @@ int autotune(cmb3d_plan_s* p, cudaStream_t s) {
       if (t < t_f) t_f = t, best.fused = v;
     }
   if (!(p->flags & CMB3D_FLAG_FUSED_YX) && t_y + t_x <= t_f) best.fused = -1;
+  if ((p->flags & CMB3D_FLAG_FP16_GEMM) && gemm_y_variant(N) >= 0) best.fused = -1, best.y = gemm_y_variant(N);
   p->sched = best;
   p->tuned = true;
   std::lock_guard<std::mutex> lock(g_tune_mu);
@@ -279,7 +304,7 @@ int run_field(cmb3d_plan_s* p, uint64_t seed, cudaStream_t s) {
     if (e != cudaSuccess) return fail_cuda(e, "yx_fused launch");
     return CMB3D_OK;
   }
-  e = timed(p, CMB3D_STAGE_YFFT, s, [&] { return cmb3d::launch_yfft(p->N, sc.y, p->buf, p->tw, s); });
+  e = timed(p, CMB3D_STAGE_YFFT, s, [&] { return launch_y(p, sc.y, s); });
   if (e != cudaSuccess) return fail_cuda(e, "yfft launch");
   e = timed(p, CMB3D_STAGE_XC2R, s, [&] { return cmb3d::launch_xc2r(p->N, sc.x, p->buf, p->tw, s); });
   if (e != cudaSuccess) return fail_cuda(e, "xc2r launch");
@@ -332,8 +357,10 @@ int cmb3d_plan(cmb3d_plan_t* out, int N, double L, double r, const double* pix_x
   if (npix > 0 && !pix_xyz) return fail(CMB3D_EINVAL, "pix_xyz is NULL");
   if (interp != CMB3D_TRILINEAR && interp != CMB3D_TRICUBIC) return fail(CMB3D_EINVAL, "interp must be 1 or 3");
   if (flags & ~uint32_t(CMB3D_FLAG_NO_SORT | CMB3D_FLAG_ALLOW_WRAP | CMB3D_FLAG_STAGE_TIMING | CMB3D_FLAG_THREE_PASS |
-                        CMB3D_FLAG_FUSED_YX | CMB3D_FLAG_AUTOTUNE))
+                        CMB3D_FLAG_FUSED_YX | CMB3D_FLAG_AUTOTUNE | CMB3D_FLAG_FP16_GEMM))
     return fail(CMB3D_EINVAL, "unknown flag bits");
+  if ((flags & CMB3D_FLAG_FP16_GEMM) && (flags & CMB3D_FLAG_FUSED_YX))
+    return fail(CMB3D_EINVAL, "CMB3D_FLAG_FP16_GEMM uses separate y and x passes");
   if ((flags & CMB3D_FLAG_THREE_PASS) && (flags & CMB3D_FLAG_FUSED_YX))
     return fail(CMB3D_EINVAL, "CMB3D_FLAG_THREE_PASS and CMB3D_FLAG_FUSED_YX exclude each other");
   for (int64_t i = 0; i < 3 * npix; ++i)
@@ -348,6 +375,13 @@ int cmb3d_plan(cmb3d_plan_t* out, int N, double L, double r, const double* pix_x
   p->flags = flags;
   p->npix = npix;
   if ((flags & CMB3D_FLAG_FUSED_YX) && cmb3d::num_fused_variants(N) > 0) p->sched.fused = 0;
+  if (flags & CMB3D_FLAG_FP16_GEMM) {
+    if (gemm_y_variant(N) < 0) {
+      delete p;
+      return fail(CMB3D_EUNSUPPORTED, "the tensor-core FFT stage exists for N = 256, 512, 1024");
+    }
+    p->sched.y = gemm_y_variant(N);
+  }
   if (cudaGetDevice(&p->device) != cudaSuccess) {
     cudaGetLastError();
     delete p;
@@ -416,11 +450,13 @@ int cmb3d_plan(cmb3d_plan_t* out, int N, double L, double r, const double* pix_x
       (st = dev_alloc(p, &p->tw, static_cast<size_t>(N), "twiddles")) != CMB3D_OK ||
       (st = dev_alloc(p, &p->tab, static_cast<size_t>(npix), "pixel table")) != CMB3D_OK ||
       (st = dev_alloc(p, &p->outbuf, static_cast<size_t>(npix), "output staging")) != CMB3D_OK ||
+      (st = dev_alloc(p, &p->d_err, 1, "error word")) != CMB3D_OK ||
       (!perm.empty() && (st = dev_alloc(p, &p->perm, perm.size(), "permutation")) != CMB3D_OK)) {
     free_plan(p);
     return st;
   }
   cudaError_t e = cudaMemcpy(p->tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(unsigned));
   if (e == cudaSuccess && npix > 0)
     e = cudaMemcpy(p->tab, tab.data(), tab.size() * sizeof(float4), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && !perm.empty())
@@ -549,7 +585,7 @@ int cmb3d_realize_sample_to_host(cmb3d_plan_t p, uint64_t seed, float* out_host,
   }
   cudaError_t e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return fail_cuda(e, "stream synchronize");
-  return CMB3D_OK;
+  return check_device_error(p);
 }
 
 namespace {
@@ -857,7 +893,7 @@ int cmb3d_stage_times(cmb3d_plan_t p, double* ms, int64_t* launches, int n, int 
     if (launches) launches[i] = i < CMB3D_NUM_STAGES ? cnt[static_cast<size_t>(i)] : 0;
   }
   if (reset) p->tnext = 0;
-  return CMB3D_OK;
+  return check_device_error(p);
 }
 
 int cmb3d_plan_schedule(cmb3d_plan_t p, int* sched) {
@@ -883,7 +919,7 @@ int cmb3d_plan_set_schedule(cmb3d_plan_t p, const int* sched) {
     sc.fused = -1;
     sc.y = sched[1];
     sc.x = sched[2];
-    if (sc.y < 0 || sc.y >= cmb3d::num_col_variants(N)) return fail(CMB3D_EINVAL, "y variant out of range");
+    if (sc.y < 0 || sc.y >= num_y_variants(N)) return fail(CMB3D_EINVAL, "y variant out of range");
     if (sc.x < 0 || sc.x >= cmb3d::num_row_variants(N)) return fail(CMB3D_EINVAL, "x variant out of range");
     if (p->flags & CMB3D_FLAG_FUSED_YX && cmb3d::num_fused_variants(N) > 0)
       return fail(CMB3D_EINVAL, "plan is restricted to the fused pass");
