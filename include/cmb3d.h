@@ -155,6 +155,17 @@ int cmb3d_fit_pk(const double* ell, const double* cl, int n, int N, double L, do
                  double* knodes_out, double* pk_out, double* fit_err);
 
 /*
+ * The forward relation on a hat basis (host only): out[i * nk + j] =
+ * 16 pi^2 int k^2 hat_j(k) j_l(k r)^2 dk for l = ell[i], so that for P_inf
+ * linear between the nodes, C_l = sum_j out[i, j] P_inf(knodes[j]) (paper
+ * Sec. II.A, Eq. 2.1 with Eq. 2.3-2.4 through the plane-wave expansion).
+ * Gauss-Legendre (16 points per node interval), Miller's recurrence for j_l.
+ *   ell     host, n integer multipoles >= 0; knodes host, nk increasing k >= 0;
+ *   out     host, n * nk doubles (row-major).
+ */
+int cmb3d_cl_matrix(const double* ell, int n, const double* knodes, int nk, double r, double* out);
+
+/*
  * Read back the plan's fitted P_inf(k) at n points (paper Sec. II.B output).
  *   k   host pointer, n abscissae (input); pk host pointer, n values (output).
  * Returns CMB3D_ENOSPEC before cmb3d_set_spectrum.

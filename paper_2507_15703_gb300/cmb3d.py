@@ -59,6 +59,7 @@ PROTOTYPES = {
     "cmb3d_set_spectrum": (_i32, [_vp, _i32, _dp, _dp, _i32, _i32, _dp]),
     "cmb3d_fit_pk": (_i32, [_dp, _dp, _i32, _i32, C.c_double, C.c_double, _i32, _dp, _dp, _dp]),
     "cmb3d_get_pk": (_i32, [_vp, _dp, _dp, _i32]),
+    "cmb3d_cl_matrix": (_i32, [_dp, _i32, _dp, _i32, C.c_double, _dp]),
     "cmb3d_realize_sample": (_i32, [_vp, _u64, _vp, _vp]),
     "cmb3d_realize_sample_to_host": (_i32, [_vp, _u64, _vp, _vp]),
     "cmb3d_realize_sample_batch": (_i32, [C.POINTER(_vp), C.POINTER(_u64), C.POINTER(_vp), _i32, _vp]),
@@ -180,6 +181,16 @@ def cmb3d_fit_pk(ell, cl, N: int, L: float, r: float, nk: int = 256):
     _check(lib.cmb3d_fit_pk(ea.ctypes.data_as(_dp), ca.ctypes.data_as(_dp), ea.size, int(N), float(L), float(r),
                             int(nk), kn.ctypes.data_as(_dp), pk.ctypes.data_as(_dp), C.byref(err)), "cmb3d_fit_pk")
     return kn, pk, err.value
+
+
+def cmb3d_cl_matrix(ell, knodes, r: float) -> np.ndarray:
+    """Forward-relation matrix A (len(ell) x len(knodes)): C_l = A @ P(knodes)."""
+    lib = load()
+    ea, ka = _f64(ell), _f64(knodes)
+    out = np.empty((ea.size, ka.size))
+    _check(lib.cmb3d_cl_matrix(ea.ctypes.data_as(_dp), ea.size, ka.ctypes.data_as(_dp), ka.size, float(r),
+                               out.ctypes.data_as(_dp)), "cmb3d_cl_matrix")
+    return out
 
 
 def cmb3d_get_pk(plan: int, k) -> np.ndarray:

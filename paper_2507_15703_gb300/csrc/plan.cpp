@@ -506,6 +506,24 @@ int cmb3d_fit_pk(const double* ell, const double* cl, int n, int N, double L, do
   return CMB3D_OK;
 }
 
+int cmb3d_cl_matrix(const double* ell, int n, const double* knodes, int nk, double r, double* out) {
+  if (!ell || !knodes || !out || n < 1 || nk < 2) return fail(CMB3D_EINVAL, "bad arrays");
+  if (!(std::isfinite(r) && r > 0)) return fail(CMB3D_EINVAL, "r must be finite and > 0");
+  for (int i = 0; i < n; ++i)
+    if (!(ell[i] >= 0) || ell[i] != std::floor(ell[i]) || ell[i] > 100000) return fail(CMB3D_EINVAL, "bad l");
+  for (int j = 0; j < nk; ++j)
+    if (!std::isfinite(knodes[j]) || knodes[j] < 0 || (j > 0 && !(knodes[j] > knodes[j - 1])))
+      return fail(CMB3D_EINVAL, "k nodes must be finite, >= 0 and increasing");
+  try {
+    std::vector<double> kn(knodes, knodes + nk);
+    std::vector<double> A = cmb3d::cl_design_matrix(ell, n, kn, r, 16);
+    std::copy(A.begin(), A.end(), out);
+  } catch (const std::bad_alloc&) {
+    return fail(CMB3D_ENOMEM, "host allocation of the design matrix");
+  }
+  return CMB3D_OK;
+}
+
 int cmb3d_set_spectrum(cmb3d_plan_t p, int kind, const double* x, const double* y, int n, int nkbins,
                        double* fit_err) {
   if (!p) return fail(CMB3D_EINVAL, "plan is NULL");

@@ -264,8 +264,17 @@ int fit_pk_from_cl(const double* ell, const double* cl, int n, int N, double L, 
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < nk; ++j)
       Aw[static_cast<size_t>(i) * nk + j] = A[static_cast<size_t>(i) * nk + j] / cl[i];
+  // Unit column norms: the non-negative solution is invariant under positive
+  // column scaling, and the normal equations become far better conditioned.
+  std::vector<double> cn(static_cast<size_t>(nk), 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < nk; ++j) cn[static_cast<size_t>(j)] += Aw[static_cast<size_t>(i) * nk + j] * Aw[static_cast<size_t>(i) * nk + j];
+  for (int j = 0; j < nk; ++j) cn[static_cast<size_t>(j)] = cn[static_cast<size_t>(j)] > 0 ? std::sqrt(cn[static_cast<size_t>(j)]) : 1.0;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < nk; ++j) Aw[static_cast<size_t>(i) * nk + j] /= cn[static_cast<size_t>(j)];
   std::vector<double> x;
   const int it = nnls(Aw, n, nk, b, 0.0, &x);
+  for (int j = 0; j < nk; ++j) x[static_cast<size_t>(j)] /= cn[static_cast<size_t>(j)];
   if (it < 0) {
     if (detail) *detail = "NNLS iteration limit reached";
     return CMB3D_EUNSUPPORTED;
