@@ -313,6 +313,58 @@ int cmb3d_plan_set_schedule(cmb3d_plan_t plan, const int* sched);
  */
 int cmb3d_batch_schedule(cmb3d_plan_t plan, int* form, int* variant);
 
+/* ------------------------------------------------------------------------
+ * Learned inversion of the angular spectrum (stands in for the NNLS fit of
+ * cmb3d_set_spectrum(CMB3D_SPEC_CL); the paper's inversion is the linear
+ * program of Sec. II.B): an MLP maps log C_l to log P_inf at fixed k nodes.
+ * Layers: `depth` hidden layers of `width` units with GELU (0.5 x (1 +
+ * erf(x / sqrt 2))), then a linear output.  Inputs are normalised as
+ * (log C_l - mu_l) / sd_l.  Training is label-free through the forward
+ * relation A (n_in x n_out, the matrix of cmb3d_cl_matrix for the same l and
+ * k nodes):  loss = mean over spectra and l of (log (A exp(y))_l - log C_l)^2.
+ * GEMMs run on the tensor cores with BF16 operands and FP32 accumulation;
+ * master weights, gradients and Adam moments are FP32.
+ * Parameter layout (flat, FP32): for each layer W (out x in, row-major) then
+ * its bias (out).
+ * ------------------------------------------------------------------------ */
+typedef struct cmb3d_mlp_s* cmb3d_mlp_t;
+
+/*
+ *   afwd       host, n_in x n_out doubles (forward relation, copied).
+ *   mu, sd     host, n_in floats each, or NULL for 0 and 1.
+ *   out_bias   host, n_out floats (initial output bias, e.g. log of a fitted
+ *              P), or NULL for 0.  Weights start N(0, 1/fan_in) from `seed`.
+ *   batch_cap  largest batch of train / loss_grad and the chunk of predict.
+ */
+int cmb3d_mlp_create(cmb3d_mlp_t* out, int n_in, int width, int depth, int n_out, const double* afwd,
+                     const float* mu, const float* sd, const float* out_bias, int batch_cap, uint64_t seed);
+
+/*
+ * Adam (beta 0.9, 0.999, eps 1e-8) over `epochs` passes of shuffled batches of
+ * `batch` rows of logcl_dev (device, n x n_in floats, log C_l); the epoch's
+ * mean loss goes to epoch_loss_host[epoch] (may be NULL).  Synchronous.
+ */
+int cmb3d_mlp_train(cmb3d_mlp_t mlp, const float* logcl_dev, int64_t n, int epochs, int batch, float lr,
+                    uint64_t seed, float* epoch_loss_host, void* stream);
+
+/* log P_inf at the nodes for n spectra: logpk_dev (device, n x n_out floats). */
+int cmb3d_mlp_predict(cmb3d_mlp_t mlp, const float* logcl_dev, int64_t n, float* logpk_dev, void* stream);
+
+/*
+ * Loss of n <= batch_cap spectra (host double) and, if grad_dev != NULL, the
+ * gradient of the loss with respect to every parameter (device, flat layout).
+ */
+int cmb3d_mlp_loss_grad(cmb3d_mlp_t mlp, const float* logcl_dev, int64_t n, double* loss_host, float* grad_dev,
+                        void* stream);
+
+/* Parameter count (*count), read (get_host) and / or write (set_host), host floats. */
+int cmb3d_mlp_params(cmb3d_mlp_t mlp, float* get_host, const float* set_host, int64_t* count);
+
+void cmb3d_mlp_destroy(cmb3d_mlp_t mlp);
+
+/* Message of the most recent MLP error on the calling thread. */
+const char* cmb3d_mlp_error_detail(void);
+
 /* Plan properties: N, number of pixels, and device bytes owned by the plan. */
 int cmb3d_plan_info(cmb3d_plan_t plan, int* N, int64_t* npix, int64_t* device_bytes);
 

@@ -384,3 +384,64 @@ def invert_cl(ell, cl, N: int, L: float, r: float, nk: int):
     x, _ = nnls(Aw, np.ones_like(cl), maxiter=50 * nk)
     err = float(np.max(np.abs(A @ x - cl) / cl))
     return knodes, x, err
+
+
+# --------------------------------------------------------------------------
+# The learned inversion's network, in FP64 (the plain definition of its
+# forward pass, loss and gradients; reference for the GPU training kernels)
+# --------------------------------------------------------------------------
+
+def mlp_shapes(n_in: int, width: int, depth: int, n_out: int):
+    """[(out, in), ...] per layer and the flat offsets of each W and bias."""
+    dims, offs, off = [], [], 0
+    for l in range(depth + 1):
+        di = n_in if l == 0 else width
+        do = n_out if l == depth else width
+        dims.append((do, di))
+        offs.append((off, off + do * di))
+        off += do * di + do
+    return dims, offs, off
+
+
+def gelu(x):
+    from scipy.special import erf
+    return 0.5 * x * (1.0 + erf(x / np.sqrt(2.0)))
+
+
+def gelu_grad(x):
+    from scipy.special import erf
+    return 0.5 * (1.0 + erf(x / np.sqrt(2.0))) + x * np.exp(-0.5 * x * x) / np.sqrt(2.0 * np.pi)
+
+
+def mlp_loss_grad(params, n_in, width, depth, n_out, A, mu, sd, logc):
+    """Loss mean((log(A exp(y)) - log C)^2) of the network with the given flat
+    parameters on spectra logc (n x n_in), and its gradient (flat), by the
+    chain rule written out layer by layer."""
+    p = np.asarray(params, dtype=np.float64)
+    dims, offs, total = mlp_shapes(n_in, width, depth, n_out)
+    Ws = [p[o:o + d[0] * d[1]].reshape(d) for d, (o, _) in zip(dims, offs)]
+    bs = [p[ob:ob + d[0]] for d, (_, ob) in zip(dims, offs)]
+    logc = np.asarray(logc, dtype=np.float64)
+    x = (logc - np.asarray(mu, np.float64)) / np.asarray(sd, np.float64)
+    zs, acts = [], [x]
+    for l in range(depth):
+        z = acts[-1] @ Ws[l].T + bs[l]
+        zs.append(z)
+        acts.append(gelu(z))
+    y = acts[-1] @ Ws[depth].T + bs[depth]
+    E = np.exp(y)
+    P = E @ np.asarray(A, np.float64).T
+    d = np.log(P) - logc
+    cnt = d.size
+    loss = float(np.sum(d * d) / cnt)
+    dP = 2.0 * d / cnt / P
+    dY = (dP @ np.asarray(A, np.float64)) * E
+    g = np.zeros(total)
+    dcur = dY
+    for l in range(depth, -1, -1):
+        o, ob = offs[l]
+        g[o:o + dims[l][0] * dims[l][1]] = (dcur.T @ acts[l]).ravel()
+        g[ob:ob + dims[l][0]] = dcur.sum(axis=0)
+        if l > 0:
+            dcur = (dcur @ Ws[l]) * gelu_grad(zs[l - 1])
+    return loss, g

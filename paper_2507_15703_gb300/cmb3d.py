@@ -73,6 +73,13 @@ PROTOTYPES = {
     "cmb3d_plan_schedule": (_i32, [_vp, C.POINTER(_i32)]),
     "cmb3d_batch_schedule": (_i32, [_vp, C.POINTER(_i32), C.POINTER(_i32)]),
     "cmb3d_plan_set_schedule": (_i32, [_vp, C.POINTER(_i32)]),
+    "cmb3d_mlp_create": (_i32, [C.POINTER(_vp), _i32, _i32, _i32, _i32, _dp, _vp, _vp, _vp, _i32, _u64]),
+    "cmb3d_mlp_train": (_i32, [_vp, _vp, _i64, _i32, _i32, C.c_float, _u64, _vp, _vp]),
+    "cmb3d_mlp_predict": (_i32, [_vp, _vp, _i64, _vp, _vp]),
+    "cmb3d_mlp_loss_grad": (_i32, [_vp, _vp, _i64, _dp, _vp, _vp]),
+    "cmb3d_mlp_params": (_i32, [_vp, _vp, _vp, C.POINTER(_i64)]),
+    "cmb3d_mlp_destroy": (None, [_vp]),
+    "cmb3d_mlp_error_detail": (C.c_char_p, []),
     "cmb3d_destroy": (None, [_vp]),
     "cmb3d_strerror": (C.c_char_p, [_i32]),
     "cmb3d_error_detail": (C.c_char_p, []),
@@ -309,6 +316,75 @@ def cmb3d_strerror(status: int) -> str:
 
 def cmb3d_error_detail() -> str:
     return load().cmb3d_error_detail().decode()
+
+
+class MlpError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        lib = load()
+        super().__init__(f"{where}: {lib.cmb3d_strerror(status).decode()} ({lib.cmb3d_mlp_error_detail().decode()})")
+
+
+def _mcheck(status: int, where: str) -> None:
+    if status != CMB3D_OK:
+        raise MlpError(status, where)
+
+
+def _f32p(a):
+    if a is None:
+        return None, None
+    arr = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    return arr, arr.ctypes.data
+
+
+def cmb3d_mlp_create(n_in, width, depth, n_out, afwd, mu=None, sd=None, out_bias=None, batch_cap=1024, seed=0):
+    lib = load()
+    A = _f64(afwd).reshape(n_in, n_out)
+    keep = [_f32p(mu), _f32p(sd), _f32p(out_bias)]
+    h = _vp()
+    _mcheck(lib.cmb3d_mlp_create(C.byref(h), int(n_in), int(width), int(depth), int(n_out), A.ctypes.data_as(_dp),
+                                 keep[0][1], keep[1][1], keep[2][1], int(batch_cap), int(seed)), "cmb3d_mlp_create")
+    return h.value
+
+
+def cmb3d_mlp_train(mlp, logcl_dev, n, epochs, batch, lr, seed=0, stream=None):
+    lib = load()
+    losses = np.zeros(max(int(epochs), 1), dtype=np.float32)
+    _mcheck(lib.cmb3d_mlp_train(mlp, _dev_ptr(logcl_dev), int(n), int(epochs), int(batch), float(lr), int(seed),
+                                losses.ctypes.data, _stream_ptr(stream)), "cmb3d_mlp_train")
+    return losses[: int(epochs)]
+
+
+def cmb3d_mlp_predict(mlp, logcl_dev, n, logpk_dev, stream=None):
+    _mcheck(load().cmb3d_mlp_predict(mlp, _dev_ptr(logcl_dev), int(n), _dev_ptr(logpk_dev), _stream_ptr(stream)),
+            "cmb3d_mlp_predict")
+
+
+def cmb3d_mlp_loss_grad(mlp, logcl_dev, n, grad_dev=None, stream=None) -> float:
+    loss = C.c_double(0.0)
+    _mcheck(load().cmb3d_mlp_loss_grad(mlp, _dev_ptr(logcl_dev), int(n), C.byref(loss), _dev_ptr(grad_dev),
+                                       _stream_ptr(stream)), "cmb3d_mlp_loss_grad")
+    return loss.value
+
+
+def cmb3d_mlp_params(mlp, set_values=None):
+    lib = load()
+    cnt = _i64()
+    _mcheck(lib.cmb3d_mlp_params(mlp, None, None, C.byref(cnt)), "cmb3d_mlp_params")
+    out = np.empty(cnt.value, dtype=np.float32)
+    if set_values is not None:
+        arr = np.ascontiguousarray(np.asarray(set_values, dtype=np.float32))
+        _mcheck(lib.cmb3d_mlp_params(mlp, None, arr.ctypes.data, None), "cmb3d_mlp_params")
+    _mcheck(lib.cmb3d_mlp_params(mlp, out.ctypes.data, None, None), "cmb3d_mlp_params")
+    return out
+
+
+def cmb3d_mlp_destroy(mlp) -> None:
+    load().cmb3d_mlp_destroy(mlp)
+
+
+def cmb3d_mlp_error_detail() -> str:
+    return load().cmb3d_mlp_error_detail().decode()
 
 
 # --------------------------------------------------------------------------
