@@ -177,6 +177,7 @@ def run_cuda(args, rank, world, local):
     w = WORKLOADS[args.workload]
     if w.batch > 1:
         return run_cuda_batch(args, rank, world, local, w)
+    learned = train_learned_inversion(args, w, dev) if w.learned else None
     pix = w.pixels()
     npix = pix.shape[0]
     ell, cl = w.cl()
@@ -190,7 +191,11 @@ def run_cuda(args, rank, world, local):
     if args.fp16_gemm:
         flags |= cmb3d.CMB3D_FLAG_FP16_GEMM
     plan = cmb3d.Plan(w.N, w.L, w.r, pix, w.interp, flags)
-    fit_err = plan.set_cl(ell, cl, w.nkbins)
+    if learned is not None:
+        plan.set_pk(learned["knodes"], learned["pk_first_heldout"])
+        fit_err = learned["summary"]["mlp_fwd_err_rms_median"]
+    else:
+        fit_err = plan.set_cl(ell, cl, w.nkbins)
     setup_s = time.time() - t0
     stream = torch.cuda.current_stream(dev)
     out = torch.empty(npix, dtype=torch.float32, device=dev)
@@ -263,9 +268,80 @@ def run_cuda(args, rank, world, local):
                            "y_pass": "split-FP16 DFT-GEMM (tcgen05)" if args.fp16_gemm else "FP32 butterflies"},
               "l2": f"no flush: per-map working set {per_map_bytes / 2**30:.2f} GiB > 129 MiB L2",
               "cl_fit_max_rel_err": fit_err, "plan_setup_s": round(setup_s, 2)}
+    if learned is not None:
+        config["cl_fit_max_rel_err"] = None
+        config["spectrum"] = "P(k) of held-out spectrum 0 from the learned inversion"
+        s = learned["summary"]
+        # a new spectrum per map: inversion time + the map's own time
+        t_map = t_max / args.steps / 1e3
+        s["maps_per_s_new_spectrum_each_map"] = {
+            "learned": round(1.0 / (t_map + s["mlp_infer_ms_per_spectrum"] / 1e3), 3),
+            "nnls": round(1.0 / (t_map + s["nnls_ms_per_spectrum"] / 1e3), 3)}
+        config["learned_inversion"] = s
     emit(args, w, value, t_max, world, config, per_map_bytes, kernels, dom, maps / e2e_s, 4 * npix,
          int(stage_n.sum()), clk)
     finish_dist(dist)
+
+
+def train_learned_inversion(args, w, dev):
+    """Train the MLP inversion on the GPU (own kernels) and judge it against
+    the library's NNLS inversion on held-out spectra of the same family."""
+    import torch
+    from paper_2507_15703_gb300 import cmb3d
+    from synth import random_cl_family
+    ell = np.arange(2, w.lmax + 1, dtype=np.float64)
+    n_hold, n_nnls = 64, 8
+    _, cl = random_cl_family(np.random.default_rng(w.train_seed), w.n_train + n_hold, w.lmax)
+    logc = np.log(cl).astype(np.float32)
+    train, hold, cl_hold = logc[: w.n_train], logc[w.n_train:], cl[w.n_train:]
+    kn = np.linspace(0.0, math.sqrt(3) * math.pi * w.N / w.L, w.nkbins)   # the NNLS nodes
+    A = cmb3d.cmb3d_cl_matrix(ell, kn, w.r)
+    mu, sd = train.mean(0), train.std(0) + 1e-3
+    out_bias = np.full(kn.size, np.log(np.mean(cl[:1000]) / np.mean(A.sum(1))), dtype=np.float32)
+    mlp = cmb3d.cmb3d_mlp_create(ell.size, 256, 3, kn.size, A, mu, sd, out_bias, batch_cap=1024, seed=w.train_seed)
+    x = torch.tensor(train, device=dev)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    # step schedule: (epochs, learning rate); Adam state carries across phases
+    schedule = [(args.train_epochs * 6 // 12, 1e-3), (args.train_epochs * 4 // 12, 3e-4),
+                (args.train_epochs - args.train_epochs * 10 // 12, 1e-4)]
+    losses = np.concatenate([cmb3d.cmb3d_mlp_train(mlp, x, w.n_train, ep, 1024, lr, seed=w.train_seed + i)
+                             for i, (ep, lr) in enumerate(schedule) if ep > 0])
+    torch.cuda.synchronize(dev)
+    train_s = time.perf_counter() - t0
+    xh = torch.tensor(hold, device=dev)
+    yh = torch.empty((n_hold, kn.size), dtype=torch.float32, device=dev)
+    cmb3d.cmb3d_mlp_predict(mlp, xh, n_hold, yh)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(10):
+        cmb3d.cmb3d_mlp_predict(mlp, xh, n_hold, yh)
+    torch.cuda.synchronize(dev)
+    infer_ms = (time.perf_counter() - t0) / (10 * n_hold) * 1e3
+    P = np.exp(yh.cpu().numpy().astype(np.float64))
+    rel = np.abs(P @ A.T - cl_hold) / cl_hold
+    cmb3d.cmb3d_mlp_destroy(mlp)
+    # the method without it: NNLS on the library's own nodes, same spectra
+    nn_rms, nn_max = [], []
+    t0 = time.perf_counter()
+    for i in range(n_nnls):
+        kk, pk, err = cmb3d.cmb3d_fit_pk(ell, cl_hold[i], w.N, w.L, w.r, w.nkbins)
+        e = np.abs(cmb3d.cmb3d_cl_matrix(ell, kk, w.r) @ pk - cl_hold[i]) / cl_hold[i]
+        nn_rms.append(float(np.sqrt(np.mean(e ** 2))))
+        nn_max.append(float(e.max()))
+    nnls_ms = (time.perf_counter() - t0) / n_nnls * 1e3
+    summary = {"train_spectra": w.n_train, "epochs": args.train_epochs, "lr_schedule": schedule,
+               "train_s": round(train_s, 2),
+               "train_spectra_per_s": round(w.n_train * args.train_epochs / train_s, 1),
+               "loss_first_last_epoch": [float(losses[0]), float(losses[-1])],
+               "net": "2047 -> 3 x 256 GELU -> 512, BF16 GEMM operands, FP32 accumulate",
+               "mlp_fwd_err_rms_median": float(np.median(np.sqrt(np.mean(rel ** 2, axis=1)))),
+               "mlp_fwd_err_max_median": float(np.median(rel.max(axis=1))),
+               "nnls_fwd_err_rms_median": float(np.median(nn_rms)),
+               "nnls_fwd_err_max_median": float(np.median(nn_max)),
+               "mlp_infer_ms_per_spectrum": round(infer_ms, 4), "nnls_ms_per_spectrum": round(nnls_ms, 1),
+               "heldout": n_hold, "nnls_heldout": n_nnls}
+    return {"knodes": kn, "pk_first_heldout": P[0], "summary": summary}
 
 
 def run_cuda_batch(args, rank, world, local, w):
@@ -520,6 +596,7 @@ def main():
     ap.add_argument("--three-pass", action="store_true", help="only separate y and x passes")
     ap.add_argument("--fused", action="store_true", help="only the fused y+x pass")
     ap.add_argument("--sweep", action="store_true", help="also time every kernel variant (stderr)")
+    ap.add_argument("--train-epochs", type=int, default=120, help="learned-inversion workload: training epochs")
     ap.add_argument("--fp16-gemm", action="store_true",
                     help="y pass with split-FP16 DFT-GEMM stages on the tensor cores")
     args = ap.parse_args()

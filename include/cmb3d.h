@@ -340,7 +340,8 @@ int cmb3d_mlp_create(cmb3d_mlp_t* out, int n_in, int width, int depth, int n_out
                      const float* mu, const float* sd, const float* out_bias, int batch_cap, uint64_t seed);
 
 /*
- * Adam (beta 0.9, 0.999, eps 1e-8) over `epochs` passes of shuffled batches of
+ * Adam (beta 0.9, 0.999, eps 1e-8, gradient clipped to global norm 1) over
+ * `epochs` passes of shuffled batches of
  * `batch` rows of logcl_dev (device, n x n_in floats, log C_l); the epoch's
  * mean loss goes to epoch_loss_host[epoch] (may be NULL).  Synchronous.
  */

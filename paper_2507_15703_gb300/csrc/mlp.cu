@@ -5,7 +5,8 @@
 // Training needs no labels: the loss is the method's own forward relation
 // (paper Sec. II.A, C_l = sum_j A[l, j] P(k_j) for P linear between nodes),
 //     loss = mean over spectra and l of (log (A exp(y))_l - log C_l)^2,
-// where y is the network output.  exp keeps P positive.
+// where y is the network output.  exp keeps P positive.  Steps are Adam with
+// the gradient clipped to global norm 1.
 //
 // Everything runs in this file's kernels: a tcgen05 BF16 x BF16 -> FP32 GEMM
 // with strided (so also transposed) FP32 operands and a bias / GELU epilogue,
@@ -30,6 +31,7 @@ constexpr int kTile = 128;                         // output tile 128 x 128
 constexpr int kKc = 64;                            // K chunk per MMA round
 constexpr uint32_t kLbo = 128, kSbo = (kKc / 8) * 128;
 constexpr uint32_t kSpin = 1u << 24;
+constexpr float kClip = 1.0f;                      // global gradient-norm clip of the Adam steps
 constexpr int kGemmSmem = 48 * 1024;               // 32 KB used; 48 KB caps residency at 4 blocks/SM,
                                                    // so 4 x 128 TMEM columns always fit
 
@@ -140,20 +142,33 @@ __global__ void k_gather_rows(const float* __restrict__ src, const long long* __
   norm[i] = (v - mu[l]) / sd[l];
 }
 
-__global__ void k_exp(const float* __restrict__ y, float* __restrict__ e, long long n) {
-  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i < n) e[i] = expf(y[i]);
+// Row maxima of y (B x n): the forward relation is evaluated as the shifted
+// log-sum-exp log(A exp(y))_l = ymax + log(A exp(y - ymax))_l, which neither
+// overflows nor changes the loss or its gradient.
+__global__ void k_rowmax(const float* __restrict__ y, int B, int n, float* __restrict__ ymax) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  float m = -INFINITY;
+  for (int j = 0; j < n; ++j) m = fmaxf(m, y[static_cast<long long>(b) * n + j]);
+  ymax[b] = m;
 }
 
-// d = log P - log C; loss += d^2; dP = 2 d / (count P)
-__global__ void k_loss(const float* __restrict__ P, const float* __restrict__ logc, long long n, float inv_count,
-                       float* __restrict__ dP, double* __restrict__ loss) {
+__global__ void k_exp(const float* __restrict__ y, const float* __restrict__ ymax, int n, float* __restrict__ e,
+                      long long total) {
+  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < total) e[i] = expf(y[i] - ymax[i / n]);
+}
+
+// d = log P - log C with log P = ymax + log P'; loss += d^2; dP' = 2 d / (count P')
+__global__ void k_loss(const float* __restrict__ P, const float* __restrict__ ymax, int L,
+                       const float* __restrict__ logc, long long n, float inv_count, float* __restrict__ dP,
+                       double* __restrict__ loss) {
   __shared__ double part[256];
   const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   double acc = 0.0;
   if (i < n) {
     const float p = fmaxf(P[i], 1e-30f);
-    const float d = logf(p) - logc[i];
+    const float d = logf(p) + ymax[i / L] - logc[i];
     acc = static_cast<double>(d) * d;
     if (dP) dP[i] = 2.0f * d * inv_count / p;
   }
@@ -185,12 +200,31 @@ __global__ void k_colsum(const float* __restrict__ x, int M, int N, float* __res
   out[n] = s;
 }
 
+// Sum of squares of the gradient (for global-norm clipping).
+__global__ void k_sqnorm(const float* __restrict__ g, long long n, double* __restrict__ out) {
+  __shared__ double part[256];
+  double acc = 0.0;
+  for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += static_cast<long long>(gridDim.x) * blockDim.x)
+    acc += static_cast<double>(g[i]) * g[i];
+  part[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) part[threadIdx.x] += part[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicAdd(out, part[0]);
+}
+
+// Adam with the gradient scaled to global norm <= clip.
 __global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m1,
                        float* __restrict__ m2, long long n, float lr, float b1, float b2, float eps, float c1,
-                       float c2) {
+                       float c2, const double* __restrict__ sqnorm, float clip) {
   const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const float gi = g[i];
+  const double nrm = sqrt(*sqnorm);
+  const float scale = nrm > clip ? static_cast<float>(clip / nrm) : 1.0f;
+  const float gi = g[i] * scale;
   const float a = b1 * m1[i] + (1.f - b1) * gi, b = b2 * m2[i] + (1.f - b2) * gi * gi;
   m1[i] = a;
   m2[i] = b;
@@ -211,9 +245,10 @@ struct cmb3d_mlp_s {
   float *afwd = nullptr, *mu = nullptr, *sd = nullptr;              // forward matrix n_in x n_out, normalisation
   std::vector<float*> z, act;                                       // per hidden layer: pre-activation, output
   float *xraw = nullptr, *xn = nullptr, *y = nullptr, *e = nullptr, *p = nullptr, *dp = nullptr, *de = nullptr;
-  float *dy = nullptr, *dg = nullptr, *dz = nullptr;
+  float *dy = nullptr, *dg = nullptr, *dz = nullptr, *ymax = nullptr;
   long long* rows = nullptr;
   double* loss = nullptr;
+  double* gnorm = nullptr;
   unsigned* err = nullptr;
   long long step = 0;
 };
@@ -255,15 +290,18 @@ cudaError_t forward(cmb3d_mlp_s* h, int B, cudaStream_t s) {
 cudaError_t loss_and_grad(cmb3d_mlp_s* h, int B, bool grads, cudaStream_t s) {
   const long long ny = static_cast<long long>(B) * h->n_out, np = static_cast<long long>(B) * h->n_in;
   cudaError_t e = forward(h, B, s);
-  if (e == cudaSuccess) k_exp<<<blocks_for(ny), 256, 0, s>>>(h->y, h->e, ny);
+  if (e == cudaSuccess) {
+    k_rowmax<<<blocks_for(B, 128), 128, 0, s>>>(h->y, B, h->n_out, h->ymax);
+    k_exp<<<blocks_for(ny), 256, 0, s>>>(h->y, h->ymax, h->n_out, h->e, ny);
+  }
   // P = E A^T: (B x n_out) times A (n_in x n_out) as the (n = l, k = j) operand
   if (e == cudaSuccess)
     e = gemm(h, B, h->n_in, h->n_out, Mat{h->e, h->n_out, 1}, Mat{h->afwd, h->n_out, 1}, 1.f, nullptr, nullptr, h->p,
              h->n_in, 1, false, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->loss, 0, sizeof(double), s);
   if (e == cudaSuccess)
-    k_loss<<<blocks_for(np), 256, 0, s>>>(h->p, h->xraw, np, 1.0f / static_cast<float>(np), grads ? h->dp : nullptr,
-                                          h->loss);
+    k_loss<<<blocks_for(np), 256, 0, s>>>(h->p, h->ymax, h->n_in, h->xraw, np, 1.0f / static_cast<float>(np),
+                                          grads ? h->dp : nullptr, h->loss);
   if (e != cudaSuccess || !grads) return e == cudaSuccess ? cudaGetLastError() : e;
   // dE = dP A ; dY = dE * E
   e = gemm(h, B, h->n_out, h->n_in, Mat{h->dp, h->n_in, 1}, Mat{h->afwd, 1, h->n_out}, 1.f, nullptr, nullptr, h->de,
@@ -305,7 +343,8 @@ void free_mlp(cmb3d_mlp_s* h) {
                   static_cast<void*>(h->y), static_cast<void*>(h->e), static_cast<void*>(h->p),
                   static_cast<void*>(h->dp), static_cast<void*>(h->de), static_cast<void*>(h->dy),
                   static_cast<void*>(h->dg), static_cast<void*>(h->dz), static_cast<void*>(h->rows),
-                  static_cast<void*>(h->loss), static_cast<void*>(h->err)})
+                  static_cast<void*>(h->loss), static_cast<void*>(h->err), static_cast<void*>(h->ymax),
+                  static_cast<void*>(h->gnorm)})
     cudaFree(p);
   for (float* p : h->z) cudaFree(p);
   for (float* p : h->act) cudaFree(p);
@@ -373,7 +412,8 @@ int cmb3d_mlp_create(cmb3d_mlp_t* out, int n_in, int width, int depth, int n_out
             cudaMalloc(&h->dp, B * n_in * 4) == cudaSuccess && cudaMalloc(&h->de, B * n_out * 4) == cudaSuccess &&
             cudaMalloc(&h->dy, B * n_out * 4) == cudaSuccess && cudaMalloc(&h->dg, B * width * 4) == cudaSuccess &&
             cudaMalloc(&h->dz, B * width * 4) == cudaSuccess && cudaMalloc(&h->rows, B * 8) == cudaSuccess &&
-            cudaMalloc(&h->loss, 8) == cudaSuccess && cudaMalloc(&h->err, 4) == cudaSuccess;
+            cudaMalloc(&h->loss, 8) == cudaSuccess && cudaMalloc(&h->err, 4) == cudaSuccess &&
+            cudaMalloc(&h->ymax, B * 4) == cudaSuccess && cudaMalloc(&h->gnorm, 8) == cudaSuccess;
   for (int l = 0; l < depth && ok; ++l) {
     float *zl = nullptr, *al = nullptr;
     ok = cudaMalloc(&zl, B * width * 4) == cudaSuccess && cudaMalloc(&al, B * width * 4) == cudaSuccess;
@@ -439,7 +479,11 @@ int cmb3d_mlp_train(cmb3d_mlp_t h, const float* logcl_dev, int64_t n, int epochs
       if (e != cudaSuccess) return mfail(CMB3D_ECUDA, cudaGetErrorString(e));
       ++h->step;
       const float c1 = 1.f - std::pow(b1, static_cast<float>(h->step)), c2 = 1.f - std::pow(b2, static_cast<float>(h->step));
-      k_adam<<<blocks_for(h->nparam), 256, 0, s>>>(h->w, h->g, h->m1, h->m2, h->nparam, lr, b1, b2, eps, c1, c2);
+      e = cudaMemsetAsync(h->gnorm, 0, sizeof(double), s);
+      if (e != cudaSuccess) return mfail(CMB3D_ECUDA, cudaGetErrorString(e));
+      k_sqnorm<<<304, 256, 0, s>>>(h->g, h->nparam, h->gnorm);
+      k_adam<<<blocks_for(h->nparam), 256, 0, s>>>(h->w, h->g, h->m1, h->m2, h->nparam, lr, b1, b2, eps, c1, c2,
+                                                     h->gnorm, kClip);
       double l = 0.0;
       e = cudaMemcpyAsync(&l, h->loss, sizeof(double), cudaMemcpyDeviceToHost, s);
       if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -102,6 +102,9 @@ class Workload:
     period: float = 22.0
     batch: int = 1          # boxes per step; > 1: each box has its own cap
     fsky_seed: int = 2507   # seed of the per-box sky fractions (batch > 1)
+    learned: bool = False   # P(k) from the learned inversion (trained per run)
+    n_train: int = 100000   # training spectra of the learned inversion
+    train_seed: int = 4     # seed of the training and held-out spectra
 
     @property
     def L(self) -> float:
@@ -129,6 +132,12 @@ WORKLOADS = {
     # of a 12*512^2-point grid, ~55M pixels in all), trilinear.
     "batch64_box256_trilinear": Workload("batch64_box256_trilinear", N=256, nside=512, fsky=0.275,
                                          lmax=128, damping=100.0, interp=1, batch=64),
+    # 2048^3 box, ~20M cap pixels, tricubic, P(k) on 512 k nodes from the
+    # learned inversion of C_l (l = 2..2048) trained on 100k spectra of the
+    # family with amplitude in [1e2, 1e4], period in [15, 30], damping in
+    # [800, 2000].
+    "box2048_cap0.4_learned": Workload("box2048_cap0.4_learned", N=2048, nside=2048, fsky=0.4,
+                                       lmax=2048, damping=1000.0, interp=3, nkbins=512, learned=True),
     # 1024^3 box, ~20M cap pixels, tricubic.
     "box1024_cap0.4_tricubic": Workload("box1024_cap0.4_tricubic", N=1024, nside=2048, fsky=0.4,
                                         lmax=768, damping=600.0, interp=3),
