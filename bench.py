@@ -190,7 +190,11 @@ def run_cuda(args, rank, world, local):
         flags |= cmb3d.CMB3D_FLAG_FUSED_YX
     if args.fp16_gemm:
         flags |= cmb3d.CMB3D_FLAG_FP16_GEMM
+    if args.schedule:
+        flags &= ~cmb3d.CMB3D_FLAG_AUTOTUNE
     plan = cmb3d.Plan(w.N, w.L, w.r, pix, w.interp, flags)
+    if args.schedule:
+        cmb3d.cmb3d_plan_set_schedule(plan.handle, tuple(int(v) for v in args.schedule.split(",")))
     if learned is not None:
         plan.set_pk(learned["knodes"], learned["pk_first_heldout"])
         fit_err = learned["summary"]["mlp_fwd_err_rms_median"]
@@ -241,6 +245,15 @@ def run_cuda(args, rank, world, local):
         cmb3d.cmb3d_realize_sample_to_host(plan.handle, seed0 + i, host, stream)
     barrier()
     e2e_s = max_over_ranks(dist, time.perf_counter() - t1, dev)
+    # the download alone (same pinned buffer, same stream), to separate the
+    # host link from the map's own time in the end-to-end figure
+    host_t = torch.from_numpy(host)
+    ev0.record(stream)
+    for i in range(args.steps):
+        host_t.copy_(out, non_blocking=True)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    d2h_ms = ev0.elapsed_time(ev1) / args.steps
     cmb3d.cmb3d_stage_times(plan.handle, reset=True)
     plan.close()
 
@@ -267,7 +280,9 @@ def run_cuda(args, rank, world, local):
                            "restriction": "three-pass" if args.three_pass else "fused" if args.fused else "autotuned",
                            "y_pass": "split-FP16 DFT-GEMM (tcgen05)" if args.fp16_gemm else "FP32 butterflies"},
               "l2": f"no flush: per-map working set {per_map_bytes / 2**30:.2f} GiB > 129 MiB L2",
-              "cl_fit_max_rel_err": fit_err, "plan_setup_s": round(setup_s, 2)}
+              "cl_fit_max_rel_err": fit_err, "plan_setup_s": round(setup_s, 2),
+              "e2e_d2h_ms_per_map": round(d2h_ms, 4),
+              "e2e_d2h_gbs": round(4 * npix / (d2h_ms / 1e3) / 1e9, 1)}
     if learned is not None:
         config["cl_fit_max_rel_err"] = None
         config["spectrum"] = "P(k) of held-out spectrum 0 from the learned inversion"
@@ -596,6 +611,8 @@ def main():
     ap.add_argument("--three-pass", action="store_true", help="only separate y and x passes")
     ap.add_argument("--fused", action="store_true", help="only the fused y+x pass")
     ap.add_argument("--sweep", action="store_true", help="also time every kernel variant (stderr)")
+    ap.add_argument("--schedule", default="",
+                    help="fixed kernel variants 'draw,y,x,fused' (fused -1: separate passes) instead of the autotuner")
     ap.add_argument("--train-epochs", type=int, default=120, help="learned-inversion workload: training epochs")
     ap.add_argument("--fp16-gemm", action="store_true",
                     help="y pass with split-FP16 DFT-GEMM stages on the tensor cores")

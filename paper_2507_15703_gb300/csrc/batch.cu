@@ -46,9 +46,9 @@ struct Sizes {
   static constexpr int D_TILES = (N2 / S::TD) * N, Y_TILES = (N2 / S::TY) * N, X_BLOCKS = N * N / ROWS;
   static constexpr int ND = D_TILES / kBatchTilesPerItem, NY = Y_TILES / kBatchTilesPerItem;
   static constexpr int NX = X_BLOCKS / kBatchTilesPerItem;
-  static constexpr int SMEM_ELEMS = (N * S::TD > N * S::TY ? N * S::TD : N * S::TY) > ROWS * P
-                                        ? (N * S::TD > N * S::TY ? N * S::TD : N * S::TY)
-                                        : ROWS * P;
+  static constexpr int DE = col_tile_elems<N, S::RD, S::TD>(), YE = col_tile_elems<N, S::RY, S::TY>();
+  static constexpr int CE = DE > YE ? DE : YE;
+  static constexpr int SMEM_ELEMS = CE > ROWS * P ? CE : ROWS * P;
   static_assert(S::TD * (N / S::RD) == kThreads && S::TY * (N / S::RY) == kThreads, "tile shapes");
   static_assert(D_TILES % kBatchTilesPerItem == 0 && X_BLOCKS % kBatchTilesPerItem == 0, "item grouping");
 };

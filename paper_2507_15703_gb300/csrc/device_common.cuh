@@ -108,15 +108,15 @@ template <> struct IDft<16> {
 
 // Philox4x32-10: ten rounds of two 32x32->64 multiplies, XOR of the high
 // halves with the round key into the other words, and a word swap; the key is
-// bumped by the two Weyl constants between rounds.
+// bumped by the two Weyl constants between rounds.  Each multiply is one
+// 64-bit product (high and low halves together).
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
 #pragma unroll
   for (int i = 0; i < 10; ++i) {
-    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
-    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
-    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
-    k.x += 0x9E3779B9u;
-    k.y += 0xBB67AE85u;
+    const uint64_t p0 = static_cast<uint64_t>(0xD2511F53u) * c.x;
+    const uint64_t p1 = static_cast<uint64_t>(0xCD9E8D57u) * c.z;
+    c = make_uint4(static_cast<uint32_t>(p1 >> 32) ^ c.y ^ (k.x + i * 0x9E3779B9u), static_cast<uint32_t>(p1),
+                   static_cast<uint32_t>(p0 >> 32) ^ c.w ^ (k.y + i * 0xBB67AE85u), static_cast<uint32_t>(p0));
   }
   return c;
 }
@@ -128,15 +128,46 @@ __device__ __forceinline__ float uniform_from_word(uint32_t w) {
   return (__uint_as_float(0x3F800000u | (w >> 9)) - 1.0f) + 5.9604644775390625e-08f;
 }
 
+// sin and cos of 2 pi u for a uniform u = (k + 1/2) 2^-23 in (0, 1).  The
+// quadrant q = nearest integer to 4u comes from the rounding of 4u + 1.5 2^23
+// (no ties: 4u is an odd multiple of 2^-22), r = u - q/4 in [-1/8, 1/8] is
+// exact, and sin(2 pi r), cos(2 pi r) are their Taylor series through r^9 and
+// r^10 (truncation below 2e-9 for |2 pi r| <= pi/4; coefficients
+// (-1)^n (2 pi)^(2n+1) / (2n+1)! and (-1)^n (2 pi)^(2n) / (2n)!); the
+// rotation by q pi/2 is a swap and sign flips.  Over all 2^23 inputs the
+// error is below 1e-7 (about 1.5 ulp of 1).
+__device__ __forceinline__ void sincos_2pi(float u, float& sn, float& cs) {
+  const float t = fmaf(4.0f, u, 12582912.0f);
+  const uint32_t q = __float_as_uint(t);
+  const float r = fmaf(-0.25f, t - 12582912.0f, u);
+  const float z = r * r;
+  float ps = fmaf(z, 42.058693944897655f, -76.70585975306139f);
+  ps = fmaf(z, ps, 81.60524927607506f);
+  ps = fmaf(z, ps, -41.34170224039976f);
+  ps = fmaf(z, ps, 6.283185307179586f);
+  const float s0 = r * ps;
+  float pc = fmaf(z, -26.4262567833744f, 60.24464137187666f);
+  pc = fmaf(z, pc, -85.45681720669373f);
+  pc = fmaf(z, pc, 64.9393940226683f);
+  pc = fmaf(z, pc, -19.739208802178716f);
+  const float c0 = fmaf(z, pc, 1.0f);
+  const uint32_t flip = (q & 2u) << 30;              // negate both in quadrants 2, 3
+  const float c1 = (q & 1u) ? -s0 : c0, s1 = (q & 1u) ? c0 : s0;
+  cs = __uint_as_float(__float_as_uint(c1) ^ flip);
+  sn = __uint_as_float(__float_as_uint(s1) ^ flip);
+}
+
 // Box-Muller: two standard normals (g1, g2) = sqrt(-2 ln u0) (cos 2 pi u1,
-// sin 2 pi u1), with the accurate logarithm and sincospi: the hardware
-// sine/cosine (about 2^-21 absolute) put the field's worst point above the
-// 1e-5 FP32-path tolerance.
+// sin 2 pi u1), with the accurate logarithm and the sin/cos above: the
+// hardware sine/cosine (about 2^-21 absolute) put the field's worst point
+// above the 1e-5 FP32-path tolerance.  The square root is s * rsqrt(s)
+// (s > 0 since u0 < 1), within 2 ulp.
 __device__ __forceinline__ float2 box_muller(uint32_t w0, uint32_t w1) {
   const float u0 = uniform_from_word(w0), u1 = uniform_from_word(w1);
-  const float rad = sqrtf(-2.0f * logf(u0));
+  const float s2 = -2.0f * logf(u0);
+  const float rad = s2 * rsqrtf(s2);
   float s, c;
-  sincospif(2.0f * u1, &s, &c);
+  sincos_2pi(u1, s, c);
   return make_float2(rad * c, rad * s);
 }
 

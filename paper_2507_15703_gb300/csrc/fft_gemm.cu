@@ -106,7 +106,8 @@ template <int N>
 struct GemmShape {
   static constexpr int T = 8, R = 16, NT = T * (N / R), MB = NT / 128, N2 = N / 2, NB = N / R;
   static constexpr int TMEM_COLS = 32 * MB < 32 ? 32 : 32 * MB;
-  static constexpr size_t SMEM = static_cast<size_t>(NT) * kRowBytes + 32 * kRowBytes + sizeof(float2) * N * T;
+  static constexpr size_t SMEM =
+      static_cast<size_t>(NT) * kRowBytes + 32 * kRowBytes + sizeof(float2) * col_tile_elems<N, R, T>();
   static_assert(NT % 128 == 0, "whole 128-row MMA blocks");
 };
 
@@ -157,7 +158,7 @@ __global__ void __launch_bounds__(GemmShape<N>::NT) k_yfft_gemm(float2* __restri
 #pragma unroll
   for (int r = 0; r < 16; ++r) v[r] = __ldcg(col + static_cast<size_t>(j + r * G::NB) * G::N2);
   stockham<N, 16, N, false>(
-      v, sm, tw, j, [&](int n) { return n * G::T + c; },
+      v, sm, tw, j, [&](int n) { return col_slot<G::R, G::T>(n, c); },
       [&](int n, float2 x) { __stcg(col + static_cast<size_t>(n) * G::N2, x); }, BlockSync{}, dft);
   tc::fence_before_sync();
   __syncthreads();

@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(T*(N / R)) k_yfft(float2* __restrict__ buf, co
 template <int N, int R, int ROWS>
 __global__ void __launch_bounds__(ROWS*(N / 2 / R)) k_xc2r(float2* __restrict__ buf, const float2* __restrict__ tw) {
   extern __shared__ float2 sm[];
-  xc2r_rows<N, R, ROWS>(buf + static_cast<size_t>(blockIdx.x) * ROWS * (N / 2), sm, tw);
+  xc2r_rows<N, R, ROWS, false>(buf + static_cast<size_t>(blockIdx.x) * ROWS * (N / 2), sm, tw);
 }
 
 // Fused y + x passes: one thread-block cluster of C blocks owns one z-plane.
@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(T*(N / RY)) k_yx_fused(float2* __restrict__ bu
 template <int N, int R, int T>
 cudaError_t run_draw_zfft(float2* buf, const float* amp, const float2* tw, uint2 key, const uint2* keyp,
                           cudaStream_t s) {
-  const size_t smem = sizeof(float2) * N * T;
+  const size_t smem = sizeof(float2) * col_tile_elems<N, R, T>();
   auto kern = k_draw_zfft<N, R, T>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
@@ -80,7 +80,7 @@ cudaError_t run_draw_zfft(float2* buf, const float* amp, const float2* tw, uint2
 
 template <int N, int R, int T>
 cudaError_t run_yfft(float2* buf, const float2* tw, cudaStream_t s) {
-  const size_t smem = sizeof(float2) * N * T;
+  const size_t smem = sizeof(float2) * col_tile_elems<N, R, T>();
   auto kern = k_yfft<N, R, T>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
@@ -128,7 +128,8 @@ template <int N, int RY, int T, int RX, int C>
 cudaError_t run_yx_fused(float2* buf, const float2* tw, cudaStream_t s) {
   constexpr int N2 = N / 2, NT = T * (N / RY), NBX = N2 / RX, ROWS = NT / NBX;
   constexpr int P = N2 + (N2 >> 4);
-  constexpr size_t smem = sizeof(float2) * (N * T > ROWS * P ? N * T : ROWS * P);
+  constexpr int CE = col_tile_elems<N, RY, T>();
+  constexpr size_t smem = sizeof(float2) * (CE > ROWS * P ? CE : ROWS * P);
   auto kern = k_yx_fused<N, RY, T, RX, C>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
@@ -159,7 +160,7 @@ inline uint2 key_of(uint64_t seed) {
 // Variant tables.  Every box size has a default shape (variant 0); sizes from
 // 256 up have alternatives (radix, tile width, threads per block) that the
 // plan's autotuner times on the device.
-//   column passes (draw + z, y):  (R, T), T * N / R threads, N * T * 8 B shared
+//   column passes (draw + z, y):  (R, T), T * N / R threads, (N + N / R) * T * 8 B shared (T < 16)
 //   row pass (x):                 (R, threads per block)
 //   fused y+x pass:               (RY, T, RX, cluster size C)
 // ---------------------------------------------------------------------------

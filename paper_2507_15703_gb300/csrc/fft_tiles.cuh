@@ -6,6 +6,20 @@
 
 namespace cmb3d {
 
+// Shared-memory slot of element n of column c in a tile of T columns
+// transformed with radix R.  For T < 16 a 16-lane half-warp spans several
+// butterflies; one pad slot per R elements puts their 64-bit accesses in
+// distinct banks in every Stockham stage (neighbouring butterflies land R + 1
+// slots apart in the first store, 1 slot apart afterwards).
+template <int R, int T>
+__host__ __device__ constexpr int col_slot(int n, int c) {
+  return (T < 16 ? n + n / R : n) * T + c;
+}
+template <int N, int R, int T>
+__host__ __device__ constexpr int col_tile_elems() {
+  return (T < 16 ? N + N / R : N) * T;
+}
+
 
 // Fourier coefficients of the modes (mx, my, mz) and (mx, my, mz + N/2),
 // mz < N/2, which share the Philox counter (mx, my, mz, 0): words (0, 1) draw
@@ -88,7 +102,7 @@ __device__ __forceinline__ void draw_zfft_tile(float2* __restrict__ buf, const f
   for (int r = 0; r < R / 2; ++r) draw_packed_pair<N>(xp, my, j + r * NB, amp, key, v[r], v[r + R / 2]);
   float2* col = buf + static_cast<size_t>(my) * N2 + xp;   // (z, my, xp) at col[z N N2]
   stockham<N, R, N, false>(
-      v, sm, tw, j, [&](int n) { return n * T + c; },
+      v, sm, tw, j, [&](int n) { return col_slot<R, T>(n, c); },
       [&](int n, float2 x) { col[static_cast<size_t>(n) * N * N2] = x; }, BlockSync{});
 }
 
@@ -106,7 +120,7 @@ __device__ __forceinline__ void yfft_tile(float2* __restrict__ plane, int x0, fl
 #pragma unroll
   for (int r = 0; r < R; ++r) v[r] = __ldcg(col + static_cast<size_t>(j + r * NB) * N2);
   stockham<N, R, N, false>(
-      v, sm, tw, j, [&](int n) { return n * T + c; },
+      v, sm, tw, j, [&](int n) { return col_slot<R, T>(n, c); },
       [&](int n, float2 x) { __stcg(col + static_cast<size_t>(n) * N2, x); }, BlockSync{});
 }
 
@@ -114,7 +128,11 @@ __device__ __forceinline__ void yfft_tile(float2* __restrict__ plane, int x0, fl
 //   Y[k] = (G[k] + conj(G[N/2-k])) + i w^k (G[k] - conj(G[N/2-k])),  w = e^{2 pi i/N},
 // with G[0], G[N/2] the real and imaginary parts of the packed entry 0, so that
 // the N/2-point inverse FFT y[n] = f(2n) + i f(2n+1) is the real row itself.
-template <int N, int R, int ROWS>
+// Thread j of a row holds G[j + r NB]; when a row's NB threads lie in one warp
+// the partner G[N/2 - k] comes from lane (NB - j) mod NB by a shuffle (entry
+// R-1-r there, or R-r for lane 0), otherwise through shared memory.
+// FIRST_SYNC: shared memory may still be read by an earlier step of the block.
+template <int N, int R, int ROWS, bool FIRST_SYNC = true>
 __device__ __forceinline__ void xc2r_rows(float2* __restrict__ rows, float2* sm, const float2* __restrict__ tw) {
   constexpr int N2 = N / 2, NB = N2 / R;
   constexpr int P = N2 + (N2 >> 4);            // row pitch: one pad slot per 16 entries
@@ -124,21 +142,42 @@ __device__ __forceinline__ void xc2r_rows(float2* __restrict__ rows, float2* sm,
   float2 v[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) v[r] = __ldcg(g + j + r * NB);     // all loads in flight at once
+  if constexpr (NB <= 32) {
+    const int src = (NB - j) & (NB - 1);
+    float2 b[R];
 #pragma unroll
-  for (int r = 0; r < R; ++r) sm[sidx(j + r * NB)] = v[r];
-  __syncthreads();
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const int k = j + r * NB;
-    if (k == 0) {
-      const float2 p = sm[sidx(0)];
-      v[r] = make_float2(p.x + p.y, p.x - p.y);
-    } else {
-      const float2 a = sm[sidx(k)], b = cconj(sm[sidx(N2 - k)]);
-      v[r] = cadd(cadd(a, b), cmul_i(cmul(__ldg(tw + k), csub(a, b))));
+    for (int r = 0; r < R; ++r) {
+      const float2 mine = j == 0 ? v[(R - r) % R] : v[R - 1 - r];
+      b[r] = make_float2(__shfl_sync(0xffffffffu, mine.x, src, NB), __shfl_sync(0xffffffffu, mine.y, src, NB));
     }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int k = j + r * NB;
+      if (k == 0) {
+        v[r] = make_float2(v[r].x + v[r].y, v[r].x - v[r].y);
+      } else {
+        const float2 a = v[r], c = cconj(b[r]);
+        v[r] = cadd(cadd(a, c), cmul_i(cmul(__ldg(tw + k), csub(a, c))));
+      }
+    }
+    stockham<N2, R, N, FIRST_SYNC>(v, sm, tw, j, sidx, [&](int n, float2 x) { g[n] = x; }, BlockSync{});
+  } else {
+#pragma unroll
+    for (int r = 0; r < R; ++r) sm[sidx(j + r * NB)] = v[r];
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int k = j + r * NB;
+      if (k == 0) {
+        const float2 p = sm[sidx(0)];
+        v[r] = make_float2(p.x + p.y, p.x - p.y);
+      } else {
+        const float2 a = sm[sidx(k)], c = cconj(sm[sidx(N2 - k)]);
+        v[r] = cadd(cadd(a, c), cmul_i(cmul(__ldg(tw + k), csub(a, c))));
+      }
+    }
+    stockham<N2, R, N, true>(v, sm, tw, j, sidx, [&](int n, float2 x) { g[n] = x; }, BlockSync{});
   }
-  stockham<N2, R, N, true>(v, sm, tw, j, sidx, [&](int n, float2 x) { g[n] = x; }, BlockSync{});
 }
 
 }  // namespace cmb3d

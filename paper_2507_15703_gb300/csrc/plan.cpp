@@ -218,27 +218,28 @@ cudaError_t timed(cmb3d_plan_s* p, int stage, cudaStream_t s, F f) {
 std::mutex g_tune_mu;
 std::map<std::pair<int, int>, Schedule> g_tune_cache;
 
+// Median of 5 individually timed launches after 2 warm-up launches.
 template <class F>
 float time_launches(cudaStream_t s, F f, bool* ok) {
-  cudaEvent_t a, b;
-  if (cudaEventCreate(&a) != cudaSuccess) {
-    *ok = false;
+  constexpr int kWarm = 2, kRuns = 5;
+  cudaEvent_t ev[kRuns + 1];
+  int made = 0;
+  *ok = true;
+  for (; made <= kRuns && *ok; ++made) *ok = cudaEventCreate(&ev[made]) == cudaSuccess;
+  if (!*ok) --made;
+  for (int i = 0; i < kWarm && *ok; ++i) *ok = f() == cudaSuccess;
+  if (*ok) *ok = cudaEventRecord(ev[0], s) == cudaSuccess;
+  for (int i = 0; i < kRuns && *ok; ++i) *ok = f() == cudaSuccess && cudaEventRecord(ev[i + 1], s) == cudaSuccess;
+  float t[kRuns] = {};
+  if (*ok) *ok = cudaEventSynchronize(ev[kRuns]) == cudaSuccess;
+  for (int i = 0; i < kRuns && *ok; ++i) *ok = cudaEventElapsedTime(&t[i], ev[i], ev[i + 1]) == cudaSuccess;
+  for (int i = 0; i < made; ++i) cudaEventDestroy(ev[i]);
+  if (!*ok) {
+    cudaGetLastError();
     return 0.f;
   }
-  if (cudaEventCreate(&b) != cudaSuccess) {
-    cudaEventDestroy(a);
-    *ok = false;
-    return 0.f;
-  }
-  float ms = 0.f;
-  *ok = f() == cudaSuccess && cudaEventRecord(a, s) == cudaSuccess;
-  for (int i = 0; i < 3 && *ok; ++i) *ok = f() == cudaSuccess;
-  *ok = *ok && cudaEventRecord(b, s) == cudaSuccess && cudaEventSynchronize(b) == cudaSuccess &&
-        cudaEventElapsedTime(&ms, a, b) == cudaSuccess;
-  cudaEventDestroy(a);
-  cudaEventDestroy(b);
-  if (!*ok) cudaGetLastError();
-  return ms / 3.f;
+  std::sort(t, t + kRuns);
+  return t[kRuns / 2];
 }
 
 int autotune(cmb3d_plan_s* p, cudaStream_t s) {
