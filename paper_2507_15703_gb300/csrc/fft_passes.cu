@@ -12,6 +12,8 @@
 // The Hermitian planes m_x = 0 and m_x = N/2 both transform to real (y, z)
 // planes, so they share the m_x' = 0 slot as T(0,.) + i T(N/2,.), which keeps
 // every row a power of two long and the buffer exactly the size of the field.
+#include <atomic>
+
 #include "fft_tiles.cuh"
 #include "internal.h"
 
@@ -24,8 +26,12 @@ __global__ void __launch_bounds__(T*(N / R)) k_draw_zfft(float2* __restrict__ bu
                                                          const float2* __restrict__ tw, uint2 key,
                                                          const uint2* __restrict__ keyp) {
   extern __shared__ float2 sm[];
-  if (keyp) key = *keyp;
-  draw_zfft_tile<N, R, T>(buf, amp, tw, key, blockIdx.x * T, blockIdx.y, sm);
+  // two copies of the body: with the key a kernel parameter its Philox round
+  // keys stay in uniform registers, computed once per thread block
+  if (keyp)
+    draw_zfft_tile<N, R, T>(buf, amp, tw, *keyp, blockIdx.x * T, blockIdx.y, sm);
+  else
+    draw_zfft_tile<N, R, T>(buf, amp, tw, key, blockIdx.x * T, blockIdx.y, sm);
 }
 
 template <int N, int R, int T>
@@ -65,6 +71,166 @@ __global__ void __launch_bounds__(T*(N / RY)) k_yx_fused(float2* __restrict__ bu
     xc2r_rows<N, RX, ROWS>(plane + static_cast<size_t>(r0) * N2, sm, tw);
     __syncthreads();
   }
+}
+
+// Fused y + x passes through distributed shared memory.  A cluster of
+// C = N/32 thread blocks holds one z-plane (N rows of N/2 packed entries) in
+// its shared memories, and the y transform is split four-step fashion as
+// N = 32 C with input row y = c + C m and output row k = k1 + 32 k2:
+//   1. block c loads its rows y = c + C m (m < 32) and transforms along m
+//      (radix 16 in registers, radix 2 between lanes l and l + 16), then
+//      multiplies entry k1 by w_N^(c k1);
+//   2. after a cluster barrier, block b forms for k1 in [b K, (b+1) K)
+//      (K = 32 / C) the C-point transforms over the C blocks' entries k1
+//      (shared::cluster loads), i.e. rows k1 + 32 k2 of the y-transformed plane;
+//   3. after a second cluster barrier (no block reads another's memory after
+//      it) block b stores its 32 complete rows in its own shared memory and
+//      runs the x pass (complex-to-real, as in xc2r_rows) on them, writing the
+//      real rows to HBM.
+// HBM sees one read and one write of the plane for both axes.
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+  asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+
+// Load the float2 at the same shared-memory offset as `local` in the block of
+// cluster rank `rank`.
+__device__ __forceinline__ float2 ld_cluster(const float2* local, uint32_t rank) {
+  const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(local));
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  float2 v;
+  asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(r) : "memory");
+  return v;
+}
+
+template <int N>
+struct DsmemShape {
+  static constexpr int N2 = N / 2, M = 32, C = N / M, K = M / C, P = N2 + (N2 >> 4), NT = N;
+  static constexpr int ITEMS = K * N2 / NT;          // step-2 transforms per thread
+  static constexpr size_t SMEM = sizeof(float2) * M * P;
+  static_assert(C >= 2 && C <= 16 && ITEMS * C == 16, "cluster shape");
+};
+
+template <int N>
+__global__ void __launch_bounds__(N, 2) k_yx_dsmem(float2* __restrict__ buf, const float2* __restrict__ tw) {
+  using D = DsmemShape<N>;
+  constexpr int N2 = D::N2, M = D::M, C = D::C, K = D::K, P = D::P;
+  extern __shared__ float2 A[];                      // 32 rows of pitch P; entry n at n + n/16
+  auto at = [](int row, int n) { return row * P + n + (n >> 4); };
+  const int t = threadIdx.x;
+  const int crank = blockIdx.x % C;                  // rank in the (C,1,1) cluster
+  float2* plane = buf + static_cast<size_t>(blockIdx.x / C) * N * N2;
+
+  {  // step 1: lanes 0-15 take even m, lanes 16-31 odd m, of 16 columns
+    const int lane = t & 31, j = lane >> 4, col = (t >> 5) * 16 + (lane & 15);
+    float2 v[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = __ldcg(plane + static_cast<size_t>(crank + C * (j + 2 * r)) * N2 + col);
+    IDft<16>::run(v);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const float2 o = make_float2(__shfl_xor_sync(0xffffffffu, v[q].x, 16), __shfl_xor_sync(0xffffffffu, v[q].y, 16));
+      const float2 e0 = j ? o : v[q], e1 = cmul(j ? v[q] : o, __ldg(tw + (N / 32) * q));
+      const int k1 = q + 16 * j;
+      A[at(k1, col)] = cmul(j ? csub(e0, e1) : cadd(e0, e1), __ldg(tw + crank * k1));
+    }
+  }
+  cluster_sync();
+  float2 w[D::ITEMS][C];
+#pragma unroll
+  for (int u = 0; u < D::ITEMS; ++u) {                // step 2
+    const int i = t + D::NT * u, k1 = crank * K + i / N2, col = i % N2;
+    const float2* src = A + at(k1, col);
+#pragma unroll
+    for (int c = 0; c < C; ++c) w[u][c] = ld_cluster(src, c);
+    IDft<C>::run(w[u]);
+  }
+  cluster_sync();
+#pragma unroll
+  for (int u = 0; u < D::ITEMS; ++u) {
+    const int i = t + D::NT * u, k1l = i / N2, col = i % N2;
+#pragma unroll
+    for (int k2 = 0; k2 < C; ++k2) A[at(k1l + K * k2, col)] = w[u][k2];
+  }
+  __syncthreads();
+  {  // step 3: x pass on local row rl = output row crank K + rl % K + 32 (rl / K)
+    constexpr int R = 16, NB = N2 / R;
+    static_assert(M * NB == D::NT, "one thread per butterfly");
+    const int j = t % NB, rl = t / NB;
+    float2* g = plane + static_cast<size_t>(crank * K + rl % K + M * (rl / K)) * N2;
+    float2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int k = j + r * NB;
+      if (k == 0) {
+        const float2 p = A[at(rl, 0)];
+        v[r] = make_float2(p.x + p.y, p.x - p.y);
+      } else {
+        const float2 a = A[at(rl, k)], b = cconj(A[at(rl, N2 - k)]);
+        v[r] = cadd(cadd(a, b), cmul_i(cmul(__ldg(tw + k), csub(a, b))));
+      }
+    }
+    stockham<N2, R, N, true>(
+        v, A, tw, j, [&](int n) { return at(rl, n); }, [&](int n, float2 x) { g[n] = x; }, BlockSync{});
+  }
+}
+
+template <int N>
+cudaLaunchConfig_t dsmem_config(float2* buf, cudaStream_t s, cudaLaunchAttribute* attr) {
+  using D = DsmemShape<N>;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(D::C * N);
+  cfg.blockDim = dim3(D::NT);
+  cfg.dynamicSmemBytes = D::SMEM;
+  cfg.stream = s;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = D::C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  (void)buf;
+  return cfg;
+}
+
+// Attributes set and the cluster shape checked against the device once per
+// process and box size: 1 = can run, 0 = cannot (no launch is attempted).
+template <int N>
+int dsmem_ready() {
+  constexpr int kMaxDevices = 64;
+  static std::atomic<int> states[kMaxDevices];       // 0 unknown, 1 no, 2 yes
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return 0;
+  }
+  const int known = states[dev].load();
+  if (known) return known - 1;
+  using D = DsmemShape<N>;
+  auto kern = k_yx_dsmem<N>;
+  int ok = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(D::SMEM)) ==
+           cudaSuccess;
+  if (ok && D::C > 8) ok = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
+  int clusters = 0;
+  if (ok) {
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = dsmem_config<N>(nullptr, nullptr, attr);
+    ok = cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg) == cudaSuccess && clusters > 0;
+  }
+  if (!ok) cudaGetLastError();
+  states[dev].store(ok ? 2 : 1);
+  return ok ? 1 : 0;
+}
+
+template <int N>
+cudaError_t run_yx_dsmem(float2* buf, const float2* tw, cudaStream_t s) {
+  if (!dsmem_ready<N>()) return cudaErrorNotSupported;
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = dsmem_config<N>(buf, s, attr);
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_yx_dsmem<N>, buf, tw);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
 }
 
 template <int N, int R, int T>
@@ -162,12 +328,19 @@ inline uint2 key_of(uint64_t seed) {
 // plan's autotuner times on the device.
 //   column passes (draw + z, y):  (R, T), T * N / R threads, (N + N / R) * T * 8 B shared (T < 16)
 //   row pass (x):                 (R, threads per block)
-//   fused y+x pass:               (RY, T, RX, cluster size C)
+//   fused y+x pass:               (RY, T, RX, cluster size C); variant 2 (N = 256, 512): the
+//                                 distributed-shared-memory form, cluster of N/32 blocks
 // ---------------------------------------------------------------------------
 
 int num_col_variants(int N) { return N >= 256 ? 3 : 1; }
 int num_row_variants(int N) { return N >= 256 ? 3 : 1; }
-int num_fused_variants(int N) { return N == 128 ? 1 : (N == 256 || N == 512 || N == 1024) ? 2 : 0; }
+int num_fused_variants(int N) { return N == 128 ? 1 : (N == 256 || N == 512) ? 3 : N == 1024 ? 2 : 0; }
+
+bool fused_variant_available(int N, int v) {
+  if (v < 0 || v >= num_fused_variants(N)) return false;
+  if (v < 2) return true;
+  return N == 256 ? dsmem_ready<256>() == 1 : N == 512 ? dsmem_ready<512>() == 1 : false;
+}
 
 #define CMB3D_COL_SWITCH(RUN, ...)                                                        \
   switch (N * 4 + v) {                                                                  \
@@ -231,6 +404,8 @@ cudaError_t launch_yx_fused(int N, int v, float2* buf, const float2* tw, cudaStr
     case 256 * 4 + 1: return run_yx_fused<256, 16, 16, 8, 8>(buf, tw, s);
     case 512 * 4: return run_yx_fused<512, 8, 16, 8, 8>(buf, tw, s);
     case 512 * 4 + 1: return run_yx_fused<512, 16, 16, 8, 8>(buf, tw, s);
+    case 256 * 4 + 2: return run_yx_dsmem<256>(buf, tw, s);
+    case 512 * 4 + 2: return run_yx_dsmem<512>(buf, tw, s);
     case 1024 * 4: return run_yx_fused<1024, 16, 16, 8, 8>(buf, tw, s);
     case 1024 * 4 + 1: return run_yx_fused<1024, 16, 8, 8, 8>(buf, tw, s);
     default: return cudaErrorNotSupported;

@@ -29,8 +29,11 @@ cudaError_t launch_draw_only(int N, float2* buf, const float* amp, uint64_t seed
 cudaError_t launch_yfft(int N, int v, float2* buf, const float2* tw, cudaStream_t s);
 
 // Fused y and x passes (one thread-block cluster per z-plane, the plane kept in
-// L2 between the two axes); num_fused_variants(N) > 0 for 128 <= N <= 1024.
+// L2 between the two axes, or for variant 2 at N = 256, 512 in the cluster's
+// distributed shared memory); num_fused_variants(N) > 0 for 128 <= N <= 1024.
 cudaError_t launch_yx_fused(int N, int v, float2* buf, const float2* tw, cudaStream_t s);
+// Whether fused variant v can run on the current device (cluster shape fits).
+bool fused_variant_available(int N, int v);
 
 // FFT along y with the radix-16 stages as split-FP16 DFT-GEMMs on the tensor
 // cores (N = 256, 512, 1024).  *err is set if an MMA-completion wait gave up.

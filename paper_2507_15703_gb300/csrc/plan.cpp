@@ -210,10 +210,10 @@ cudaError_t timed(cmb3d_plan_s* p, int stage, cudaStream_t s, F f) {
   return cudaEventRecord(r.b, s);
 }
 
-// Autotuner: time every kernel variant of this box size once (1 warm-up and
-// 3 timed launches each, CUDA events on the caller's stream) and keep the
-// fastest draw, y and x variants and, where available, the fastest fused y+x
-// variant if it beats the best separate pair.  Results are cached per
+// Autotuner: time every kernel variant of this box size that can run on the
+// device (median of 5 launches after 2 warm-ups, CUDA events on the caller's
+// stream) and keep the fastest draw, y and x variants and, where available,
+// the fastest fused y+x variant if it beats the best separate pair.  Results are cached per
 // (device, N, flag restriction) for the life of the process.
 std::mutex g_tune_mu;
 std::map<std::pair<int, int>, Schedule> g_tune_cache;
@@ -276,6 +276,7 @@ int autotune(cmb3d_plan_s* p, cudaStream_t s) {
   }
   if (!(p->flags & CMB3D_FLAG_THREE_PASS))
     for (int v = 0; v < cmb3d::num_fused_variants(N); ++v) {
+      if (!cmb3d::fused_variant_available(N, v)) continue;
       const float t = time_launches(s, [&] { return cmb3d::launch_yx_fused(N, v, p->buf, p->tw, s); }, &ok);
       if (!ok) return fail_cuda(cudaErrorLaunchFailure, "autotune yx_fused");
       if (t < t_f) t_f = t, best.fused = v;
@@ -933,6 +934,8 @@ int cmb3d_plan_set_schedule(cmb3d_plan_t p, const int* sched) {
   if (sc.draw < 0 || sc.draw >= cmb3d::num_col_variants(N)) return fail(CMB3D_EINVAL, "draw variant out of range");
   if (sc.fused >= 0) {
     if (sc.fused >= cmb3d::num_fused_variants(N)) return fail(CMB3D_EINVAL, "fused variant out of range");
+    if (!cmb3d::fused_variant_available(N, sc.fused))
+      return fail(CMB3D_EUNSUPPORTED, "fused variant cannot run on this device (cluster shape)");
     if (p->flags & CMB3D_FLAG_THREE_PASS) return fail(CMB3D_EINVAL, "plan is restricted to separate passes");
   } else {
     sc.fused = -1;

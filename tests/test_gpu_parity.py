@@ -120,6 +120,33 @@ def test_fused_yx_pass_matches_three_pass_and_oracle(N):
 
 
 @pytest.mark.parametrize("N", [256, 512])
+def test_dsmem_fused_pass_matches_three_pass_and_oracle(N):
+    """Fused variant 2: the y+x passes of one z-plane in the distributed shared
+    memory of a cluster of N/32 blocks (four-step y transform).  Its
+    arithmetic differs from the separate passes (32 x N/32 instead of radix-16
+    stages), so both are compared with the oracle and with each other at the
+    FP32 tolerance."""
+    L = 2.2
+    kn, pk = smooth_pk(N, L)
+    pix = fibonacci_sphere(20000, 7001)
+    pb = orc.p_box_of_q(N, L, kn, pk)
+    with cmb3d.Plan(N, L, 1.0, pix, 3, cmb3d.CMB3D_FLAG_STAGE_TIMING) as plan:
+        plan.set_pk(kn, pk)
+        cmb3d.cmb3d_plan_set_schedule(plan.handle, (0, -1, -1, 2))
+        a = plan.realize_sample(11).cpu().numpy()
+        _, counts = cmb3d.cmb3d_stage_times(plan.handle)
+        assert list(counts) == [1, 0, 0, 1, 1]
+        field = plan.realize_field(12).cpu().numpy() if N == 256 else None
+        cmb3d.cmb3d_plan_set_schedule(plan.handle, (0, 0, 0, -1))
+        b = plan.realize_sample(11).cpu().numpy()
+    assert rel_err(a, b.astype(np.float64)) <= TOL
+    ref = orc.realize_sample(N, L, 1.0, pix, pb, 11, 3)
+    assert rel_err(a, ref) <= TOL
+    if field is not None:
+        assert rel_err(field, orc.realize_field(N, pb, 12)) <= TOL
+
+
+@pytest.mark.parametrize("N", [256, 512])
 def test_every_kernel_variant_matches_oracle(N):
     """Each radix / tile / thread-count variant the autotuner may pick."""
     L = 2.2
@@ -127,7 +154,7 @@ def test_every_kernel_variant_matches_oracle(N):
     pix = fibonacci_sphere(20000, 6007)
     ref = orc.realize_sample(N, L, 1.0, pix, orc.p_box_of_q(N, L, kn, pk), 17, 3)
     scheds = [(d, 0, 0, -1) for d in range(3)] + [(0, y, 0, -1) for y in range(3)] + \
-             [(0, 0, x, -1) for x in range(3)] + [(0, -1, -1, f) for f in range(2)]
+             [(0, 0, x, -1) for x in range(3)] + [(0, -1, -1, f) for f in range(3)]
     with cmb3d.Plan(N, L, 1.0, pix, 3) as plan:
         plan.set_pk(kn, pk)
         for sc in scheds:
