@@ -154,14 +154,18 @@ def ncu_traffic(kernel: str, workload: str):
     return e.get("dram_bytes_per_launch")
 
 
-def algorithmic_bytes(N: int, npix: int) -> dict:
+def algorithmic_bytes(N: int, npix: int, planes: int | None = None, rows: int | None = None) -> dict:
     """Bytes each kernel must move per launch (the packed half spectrum and the
-    real field are both 4 N^3 bytes): draw_zfft writes it once; yfft and xc2r
-    read and write it once; gather reads 16 B of table + 4 B of permutation per
-    pixel and writes 4 B per pixel (field reads are cache-dependent and not
-    counted)."""
-    box = 4 * N ** 3
-    return {"draw_zfft": box, "yfft": 2 * box, "xc2r": 2 * box, "gather": 24 * npix, "yx_fused": 2 * box}
+    real field are both 4 N^3 bytes, a row 4 N bytes): draw_zfft writes the
+    box once; yfft reads its z-planes and writes its rows; xc2r reads and
+    writes its rows; gather reads 16 B of table + 4 B of permutation per pixel
+    and writes 4 B per pixel (field reads are cache-dependent and not counted).
+    planes, rows: the pruned extent of the sky-map path (default: whole box)."""
+    box, row = 4 * N ** 3, 4 * N
+    planes = N if planes is None else planes
+    rows = N * N if rows is None else rows
+    return {"draw_zfft": box, "yfft": planes * N * row + rows * row, "xc2r": 2 * rows * row,
+            "gather": 24 * npix, "yx_fused": 2 * box}
 
 
 # --------------------------------------------------------------------------
@@ -190,6 +194,8 @@ def run_cuda(args, rank, world, local):
         flags |= cmb3d.CMB3D_FLAG_FUSED_YX
     if args.fp16_gemm:
         flags |= cmb3d.CMB3D_FLAG_FP16_GEMM
+    if args.no_prune:
+        flags |= cmb3d.CMB3D_FLAG_NO_PRUNE
     if args.schedule:
         flags &= ~cmb3d.CMB3D_FLAG_AUTOTUNE
     plan = cmb3d.Plan(w.N, w.L, w.r, pix, w.interp, flags)
@@ -235,6 +241,7 @@ def run_cuda(args, rank, world, local):
     ms = ev0.elapsed_time(ev1)
     stage_ms, stage_n = cmb3d.cmb3d_stage_times(plan.handle, reset=True)
     t_max = max_over_ranks(dist, ms, dev)
+    n_planes, n_rows = cmb3d.cmb3d_plan_prune_info(plan.handle)
 
     # end to end through the host-buffer entry point (map copied to pinned host memory)
     host = torch.empty(npix, dtype=torch.float32).pin_memory().numpy()
@@ -263,7 +270,7 @@ def run_cuda(args, rank, world, local):
 
     maps = world * args.steps
     value = maps / (t_max / 1e3)
-    ab = algorithmic_bytes(w.N, npix)
+    ab = algorithmic_bytes(w.N, npix, n_planes, n_rows)
     names = cmb3d.STAGE_NAMES
     kernels = {}
     for i, name in enumerate(names):
@@ -279,6 +286,9 @@ def run_cuda(args, rank, world, local):
               "schedule": {"draw": schedule[0], "y": schedule[1], "x": schedule[2], "fused_yx": schedule[3],
                            "restriction": "three-pass" if args.three_pass else "fused" if args.fused else "autotuned",
                            "y_pass": "split-FP16 DFT-GEMM (tcgen05)" if args.fp16_gemm else "FP32 butterflies"},
+              "pruned_transform": {"z_planes": n_planes, "rows": n_rows, "of_planes": w.N, "of_rows": w.N ** 2,
+                                   "note": "y pass on the z-planes, x pass on the (z, y) rows the "
+                                           "interpolation stencils read; maps equal the whole-box maps bit for bit"},
               "l2": f"no flush: per-map working set {per_map_bytes / 2**30:.2f} GiB > 129 MiB L2",
               "cl_fit_max_rel_err": fit_err, "plan_setup_s": round(setup_s, 2),
               "e2e_d2h_ms_per_map": round(d2h_ms, 4),
@@ -610,6 +620,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--three-pass", action="store_true", help="only separate y and x passes")
     ap.add_argument("--fused", action="store_true", help="only the fused y+x pass")
+    ap.add_argument("--no-prune", action="store_true", help="transform the whole box for every map")
     ap.add_argument("--sweep", action="store_true", help="also time every kernel variant (stderr)")
     ap.add_argument("--schedule", default="",
                     help="fixed kernel variants 'draw,y,x,fused' (fused -1: separate passes) instead of the autotuner")

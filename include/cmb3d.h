@@ -73,10 +73,15 @@ enum {
   CMB3D_FLAG_AUTOTUNE = 1u << 5,      /* at the first realization, time every kernel
                                          shape of this N and keep the fastest (cached
                                          per device and N for the process)            */
-  CMB3D_FLAG_FP16_GEMM = 1u << 6      /* y pass with its radix-16 stages as split-FP16
+  CMB3D_FLAG_FP16_GEMM = 1u << 6,     /* y pass with its radix-16 stages as split-FP16
                                          (hi+lo) DFT-GEMMs on the tensor cores, FP32
                                          accumulation (N = 256, 512, 1024; else
                                          CMB3D_EUNSUPPORTED); tolerance 1e-3 of rms    */
+  CMB3D_FLAG_NO_PRUNE = 1u << 7       /* sky maps transform the whole box: by default
+                                         (N >= 128) the y pass covers only the z-planes
+                                         and stores only the (z, y) rows, and the x pass
+                                         only the rows, that the pixels' interpolation
+                                         stencils read; the maps are identical          */
 };
 
 /* Spectrum kinds for cmb3d_set_spectrum. */
@@ -368,6 +373,17 @@ const char* cmb3d_mlp_error_detail(void);
 
 /* Plan properties: N, number of pixels, and device bytes owned by the plan. */
 int cmb3d_plan_info(cmb3d_plan_t plan, int* N, int64_t* npix, int64_t* device_bytes);
+
+/*
+ * Extent of the pruned transform a sky map uses (the paper sizes its box to
+ * the cap, Sec. II.C; here the cubic box is kept and only the part the
+ * pixels' interpolation stencils read is transformed): *planes = z-planes the
+ * y pass covers, *rows = (z, y) rows the x pass covers.  Without pruning
+ * (CMB3D_FLAG_NO_PRUNE, N < 128, or stencils touching every row) N and N^2.
+ * cmb3d_realize_field always transforms the whole box.  Host pointers; either
+ * may be NULL.
+ */
+int cmb3d_plan_prune_info(cmb3d_plan_t plan, int64_t* planes, int64_t* rows);
 
 /* Release the plan and all device memory it owns (NULL is ignored). */
 void cmb3d_destroy(cmb3d_plan_t plan);

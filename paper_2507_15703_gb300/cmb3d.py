@@ -34,6 +34,7 @@ CMB3D_FLAG_THREE_PASS = 1 << 3
 CMB3D_FLAG_FUSED_YX = 1 << 4
 CMB3D_FLAG_AUTOTUNE = 1 << 5
 CMB3D_FLAG_FP16_GEMM = 1 << 6
+CMB3D_FLAG_NO_PRUNE = 1 << 7
 
 CMB3D_SPEC_PK = 0
 CMB3D_SPEC_CL = 1
@@ -70,6 +71,7 @@ PROTOTYPES = {
     "cmb3d_stage_times": (_i32, [_vp, _dp, C.POINTER(_i64), _i32, _i32]),
     "cmb3d_realize_sample_noalloc": (_i32, [_i32, C.c_double, C.c_double, _vp, _i64, _i32, _vp, _u64, _vp, _vp]),
     "cmb3d_plan_info": (_i32, [_vp, C.POINTER(_i32), C.POINTER(_i64), C.POINTER(_i64)]),
+    "cmb3d_plan_prune_info": (_i32, [_vp, C.POINTER(_i64), C.POINTER(_i64)]),
     "cmb3d_plan_schedule": (_i32, [_vp, C.POINTER(_i32)]),
     "cmb3d_batch_schedule": (_i32, [_vp, C.POINTER(_i32), C.POINTER(_i32)]),
     "cmb3d_plan_set_schedule": (_i32, [_vp, C.POINTER(_i32)]),
@@ -282,6 +284,14 @@ def cmb3d_plan_info(plan: int) -> tuple[int, int, int]:
     n, npix, nbytes = _i32(), _i64(), _i64()
     _check(lib.cmb3d_plan_info(plan, C.byref(n), C.byref(npix), C.byref(nbytes)), "cmb3d_plan_info")
     return n.value, npix.value, nbytes.value
+
+
+def cmb3d_plan_prune_info(plan: int) -> tuple[int, int]:
+    """(z-planes, (z, y) rows) the sky-map path transforms."""
+    lib = load()
+    planes, rows = _i64(), _i64()
+    _check(lib.cmb3d_plan_prune_info(plan, C.byref(planes), C.byref(rows)), "cmb3d_plan_prune_info")
+    return planes.value, rows.value
 
 
 def cmb3d_plan_schedule(plan: int) -> tuple[int, int, int, int]:

@@ -34,16 +34,31 @@ __global__ void __launch_bounds__(T*(N / R)) k_draw_zfft(float2* __restrict__ bu
     draw_zfft_tile<N, R, T>(buf, amp, tw, key, blockIdx.x * T, blockIdx.y, sm);
 }
 
+// y pass over z-planes blockIdx.y, or with `planes` over planes[blockIdx.y];
+// with `rowmask` (N bits per plane) only the marked rows are stored.
 template <int N, int R, int T>
-__global__ void __launch_bounds__(T*(N / R)) k_yfft(float2* __restrict__ buf, const float2* __restrict__ tw) {
+__global__ void __launch_bounds__(T*(N / R)) k_yfft(float2* __restrict__ buf, const float2* __restrict__ tw,
+                                                    const int32_t* __restrict__ planes,
+                                                    const uint32_t* __restrict__ rowmask) {
   extern __shared__ float2 sm[];
-  yfft_tile<N, R, T>(buf + static_cast<size_t>(blockIdx.y) * N * (N / 2), blockIdx.x * T, sm, tw);
+  constexpr int W = N / 32 > 0 ? N / 32 : 1;
+  __shared__ uint32_t smask[W];
+  const int z = planes ? __ldg(planes + blockIdx.y) : static_cast<int>(blockIdx.y);
+  if (rowmask) {
+    for (int i = threadIdx.x; i < W; i += blockDim.x) smask[i] = __ldg(rowmask + static_cast<size_t>(z) * W + i);
+    __syncthreads();
+  }
+  yfft_tile<N, R, T>(buf + static_cast<size_t>(z) * N * (N / 2), blockIdx.x * T, sm, tw, rowmask ? smask : nullptr);
 }
 
 template <int N, int R, int ROWS>
-__global__ void __launch_bounds__(ROWS*(N / 2 / R)) k_xc2r(float2* __restrict__ buf, const float2* __restrict__ tw) {
+__global__ void __launch_bounds__(ROWS*(N / 2 / R)) k_xc2r(float2* __restrict__ buf, const float2* __restrict__ tw,
+                                                              const int32_t* __restrict__ rows) {
   extern __shared__ float2 sm[];
-  xc2r_rows<N, R, ROWS, false>(buf + static_cast<size_t>(blockIdx.x) * ROWS * (N / 2), sm, tw);
+  if (rows)
+    xc2r_rows<N, R, ROWS, false>(buf, sm, tw, rows + static_cast<size_t>(blockIdx.x) * ROWS);
+  else
+    xc2r_rows<N, R, ROWS, false>(buf + static_cast<size_t>(blockIdx.x) * ROWS * (N / 2), sm, tw);
 }
 
 // Fused y + x passes: one thread-block cluster of C blocks owns one z-plane.
@@ -245,26 +260,33 @@ cudaError_t run_draw_zfft(float2* buf, const float* amp, const float2* tw, uint2
 }
 
 template <int N, int R, int T>
-cudaError_t run_yfft(float2* buf, const float2* tw, cudaStream_t s) {
+cudaError_t run_yfft(float2* buf, const float2* tw, cudaStream_t s, const int32_t* planes, int nplanes,
+                     const uint32_t* rowmask) {
   const size_t smem = sizeof(float2) * col_tile_elems<N, R, T>();
   auto kern = k_yfft<N, R, T>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
-  kern<<<dim3(N / 2 / T, N), T * (N / R), smem, s>>>(buf, tw);
+  const int nz = planes ? nplanes : N;
+  if (nz <= 0) return cudaSuccess;
+  kern<<<dim3(N / 2 / T, nz), T * (N / R), smem, s>>>(buf, tw, planes, rowmask);
   return cudaGetLastError();
 }
 
 template <int N, int R, int THREADS>
-cudaError_t run_xc2r(float2* buf, const float2* tw, cudaStream_t s) {
+cudaError_t run_xc2r(float2* buf, const float2* tw, cudaStream_t s, const int32_t* rows, int64_t nrows) {
   constexpr int N2 = N / 2, NB = N2 / R;
   constexpr int ROWS0 = THREADS / NB > 0 ? THREADS / NB : 1;
   constexpr int ROWS = ROWS0 < N * N ? ROWS0 : N * N;
+  static_assert(N < 128 || kRowListPad % ROWS == 0, "row lists are padded to whole blocks of every row variant");
   constexpr int P = N2 + (N2 >> 4);
   const size_t smem = sizeof(float2) * P * ROWS;
   auto kern = k_xc2r<N, R, ROWS>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
-  kern<<<dim3(N * N / ROWS), ROWS * NB, smem, s>>>(buf, tw);
+  if (rows && N < 128) return cudaErrorNotSupported;
+  if (rows && (nrows <= 0 || nrows % kRowListPad != 0)) return nrows == 0 ? cudaSuccess : cudaErrorInvalidValue;
+  const int64_t nb = rows ? nrows / ROWS : static_cast<int64_t>(N) * N / ROWS;
+  kern<<<dim3(static_cast<unsigned>(nb)), ROWS * NB, smem, s>>>(buf, tw, rows);
   return cudaGetLastError();
 }
 
@@ -370,29 +392,31 @@ cudaError_t launch_draw_zfft(int N, int v, float2* buf, const float* amp, const 
   CMB3D_COL_SWITCH(run_draw_zfft, buf, amp, tw, key, key_dev, s)
 }
 
-cudaError_t launch_yfft(int N, int v, float2* buf, const float2* tw, cudaStream_t s) {
-  CMB3D_COL_SWITCH(run_yfft, buf, tw, s)
+cudaError_t launch_yfft(int N, int v, float2* buf, const float2* tw, cudaStream_t s, const int32_t* planes,
+                        int nplanes, const uint32_t* rowmask) {
+  CMB3D_COL_SWITCH(run_yfft, buf, tw, s, planes, nplanes, rowmask)
 }
 
-cudaError_t launch_xc2r(int N, int v, float2* buf, const float2* tw, cudaStream_t s) {
+cudaError_t launch_xc2r(int N, int v, float2* buf, const float2* tw, cudaStream_t s, const int32_t* rows,
+                        int64_t nrows) {
   switch (N * 4 + v) {
-    case 8 * 4: return run_xc2r<8, 4, 256>(buf, tw, s);
-    case 16 * 4: return run_xc2r<16, 8, 256>(buf, tw, s);
-    case 32 * 4: return run_xc2r<32, 8, 256>(buf, tw, s);
-    case 64 * 4: return run_xc2r<64, 8, 256>(buf, tw, s);
-    case 128 * 4: return run_xc2r<128, 8, 256>(buf, tw, s);
-    case 256 * 4: return run_xc2r<256, 8, 256>(buf, tw, s);
-    case 256 * 4 + 1: return run_xc2r<256, 16, 256>(buf, tw, s);
-    case 256 * 4 + 2: return run_xc2r<256, 8, 512>(buf, tw, s);
-    case 512 * 4: return run_xc2r<512, 8, 256>(buf, tw, s);
-    case 512 * 4 + 1: return run_xc2r<512, 16, 256>(buf, tw, s);
-    case 512 * 4 + 2: return run_xc2r<512, 8, 512>(buf, tw, s);
-    case 1024 * 4: return run_xc2r<1024, 8, 256>(buf, tw, s);
-    case 1024 * 4 + 1: return run_xc2r<1024, 16, 256>(buf, tw, s);
-    case 1024 * 4 + 2: return run_xc2r<1024, 8, 512>(buf, tw, s);
-    case 2048 * 4: return run_xc2r<2048, 16, 256>(buf, tw, s);
-    case 2048 * 4 + 1: return run_xc2r<2048, 16, 512>(buf, tw, s);
-    case 2048 * 4 + 2: return run_xc2r<2048, 8, 512>(buf, tw, s);
+    case 8 * 4: return run_xc2r<8, 4, 256>(buf, tw, s, rows, nrows);
+    case 16 * 4: return run_xc2r<16, 8, 256>(buf, tw, s, rows, nrows);
+    case 32 * 4: return run_xc2r<32, 8, 256>(buf, tw, s, rows, nrows);
+    case 64 * 4: return run_xc2r<64, 8, 256>(buf, tw, s, rows, nrows);
+    case 128 * 4: return run_xc2r<128, 8, 256>(buf, tw, s, rows, nrows);
+    case 256 * 4: return run_xc2r<256, 8, 256>(buf, tw, s, rows, nrows);
+    case 256 * 4 + 1: return run_xc2r<256, 16, 256>(buf, tw, s, rows, nrows);
+    case 256 * 4 + 2: return run_xc2r<256, 8, 512>(buf, tw, s, rows, nrows);
+    case 512 * 4: return run_xc2r<512, 8, 256>(buf, tw, s, rows, nrows);
+    case 512 * 4 + 1: return run_xc2r<512, 16, 256>(buf, tw, s, rows, nrows);
+    case 512 * 4 + 2: return run_xc2r<512, 8, 512>(buf, tw, s, rows, nrows);
+    case 1024 * 4: return run_xc2r<1024, 8, 256>(buf, tw, s, rows, nrows);
+    case 1024 * 4 + 1: return run_xc2r<1024, 16, 256>(buf, tw, s, rows, nrows);
+    case 1024 * 4 + 2: return run_xc2r<1024, 8, 512>(buf, tw, s, rows, nrows);
+    case 2048 * 4: return run_xc2r<2048, 16, 256>(buf, tw, s, rows, nrows);
+    case 2048 * 4 + 1: return run_xc2r<2048, 16, 512>(buf, tw, s, rows, nrows);
+    case 2048 * 4 + 2: return run_xc2r<2048, 8, 512>(buf, tw, s, rows, nrows);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -109,10 +109,11 @@ __device__ __forceinline__ void draw_zfft_tile(float2* __restrict__ buf, const f
 // In-place inverse FFT along y of the T adjacent columns x0 .. x0+T-1 of one
 // z-plane (plane points at element (z, 0, 0)); blockDim.x == T * N / R.
 // Loads and stores go through L2 only (.cg), so the data may have been written
-// by other thread blocks of the same cluster.
+// by other thread blocks of the same cluster.  With `mask` (N bits, shared
+// memory, visible to every thread) only rows y whose bit is set are stored.
 template <int N, int R, int T>
 __device__ __forceinline__ void yfft_tile(float2* __restrict__ plane, int x0, float2* sm,
-                                          const float2* __restrict__ tw) {
+                                          const float2* __restrict__ tw, const uint32_t* mask = nullptr) {
   constexpr int N2 = N / 2, NB = N / R;
   const int c = threadIdx.x % T, j = threadIdx.x / T;
   float2* col = plane + x0 + c;                                   // (y, x0 + c) at col[y N2]
@@ -121,7 +122,10 @@ __device__ __forceinline__ void yfft_tile(float2* __restrict__ plane, int x0, fl
   for (int r = 0; r < R; ++r) v[r] = __ldcg(col + static_cast<size_t>(j + r * NB) * N2);
   stockham<N, R, N, false>(
       v, sm, tw, j, [&](int n) { return col_slot<R, T>(n, c); },
-      [&](int n, float2 x) { __stcg(col + static_cast<size_t>(n) * N2, x); }, BlockSync{});
+      [&](int n, float2 x) {
+        if (!mask || ((mask[n >> 5] >> (n & 31)) & 1u)) __stcg(col + static_cast<size_t>(n) * N2, x);
+      },
+      BlockSync{});
 }
 
 // Row pass: for k in [0, N/2) the half-length input is
@@ -132,12 +136,15 @@ __device__ __forceinline__ void yfft_tile(float2* __restrict__ plane, int x0, fl
 // the partner G[N/2 - k] comes from lane (NB - j) mod NB by a shuffle (entry
 // R-1-r there, or R-r for lane 0), otherwise through shared memory.
 // FIRST_SYNC: shared memory may still be read by an earlier step of the block.
+// The block's rows are rows[0 .. ROWS-1] (consecutive), or with `list` the rows
+// rows + list[rl] * N/2 for rl < ROWS.
 template <int N, int R, int ROWS, bool FIRST_SYNC = true>
-__device__ __forceinline__ void xc2r_rows(float2* __restrict__ rows, float2* sm, const float2* __restrict__ tw) {
+__device__ __forceinline__ void xc2r_rows(float2* __restrict__ rows, float2* sm, const float2* __restrict__ tw,
+                                          const int32_t* __restrict__ list = nullptr) {
   constexpr int N2 = N / 2, NB = N2 / R;
   constexpr int P = N2 + (N2 >> 4);            // row pitch: one pad slot per 16 entries
   const int j = threadIdx.x % NB, rl = threadIdx.x / NB;
-  float2* g = rows + static_cast<size_t>(rl) * N2;
+  float2* g = rows + static_cast<size_t>(list ? __ldg(list + rl) : rl) * N2;
   auto sidx = [&](int n) { return rl * P + n + (n >> 4); };
   float2 v[R];
 #pragma unroll

@@ -26,7 +26,11 @@ cudaError_t launch_draw_zfft(int N, int v, float2* buf, const float* amp, const 
 cudaError_t launch_draw_only(int N, float2* buf, const float* amp, uint64_t seed, cudaStream_t s);
 
 // Inverse FFT of every (z, m_x') column along y, in place.
-cudaError_t launch_yfft(int N, int v, float2* buf, const float2* tw, cudaStream_t s);
+// With `planes` only the nplanes listed z-planes are transformed, and with
+// `rowmask` (N bits per z-plane, bit y of word z N/32 + y/32) only the marked
+// rows of them are stored.
+cudaError_t launch_yfft(int N, int v, float2* buf, const float2* tw, cudaStream_t s, const int32_t* planes = nullptr,
+                        int nplanes = 0, const uint32_t* rowmask = nullptr);
 
 // Fused y and x passes (one thread-block cluster per z-plane, the plane kept in
 // L2 between the two axes, or for variant 2 at N = 256, 512 in the cluster's
@@ -41,7 +45,11 @@ bool yfft_gemm_supported(int N);
 cudaError_t launch_yfft_gemm(int N, float2* buf, const float2* tw, unsigned* err, cudaStream_t s);
 
 // Complex-to-real inverse FFT of every (z, y) row along x, in place.
-cudaError_t launch_xc2r(int N, int v, float2* buf, const float2* tw, cudaStream_t s);
+// With `rows` (N >= 128; row indices z N + y, nrows a multiple of kRowListPad)
+// only the listed rows are transformed; padding entries must name a scratch row.
+constexpr int kRowListPad = 64;
+cudaError_t launch_xc2r(int N, int v, float2* buf, const float2* tw, cudaStream_t s, const int32_t* rows = nullptr,
+                        int64_t nrows = 0);
 
 // Interpolate the field float[z][y][x] at npix pixels.  tab[i] = (tx, ty, tz,
 // packed base cell) in gather order; out[perm[i]] receives pixel i (perm may

@@ -114,6 +114,14 @@ struct cmb3d_plan_s {
   BatchCtx batch;
   std::vector<const void*> batch_tuned_sig;   // plan set + outputs the batch autotune ran on
   int batch_best_form = 0, batch_best_v = 0;
+  // Pruned transform of the sky-map path: the z-planes and (z, y) rows the
+  // pixels' interpolation stencils read.  buf holds one scratch row past the
+  // box (row index N^2) that pads the row list.
+  bool prune = false;
+  int64_t nplanes = 0, nrows = 0, nrows_pad = 0;
+  int32_t* d_planes = nullptr;
+  int32_t* d_rows = nullptr;
+  uint32_t* d_rowmask = nullptr;   // N bits per z-plane
 };
 
 namespace {
@@ -155,6 +163,9 @@ void free_plan(cmb3d_plan_s* p) {
   cudaFree(p->perm);
   cudaFree(p->outbuf);
   cudaFree(p->d_err);
+  cudaFree(p->d_planes);
+  cudaFree(p->d_rows);
+  cudaFree(p->d_rowmask);
   for (auto& r : p->recs) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -291,7 +302,10 @@ int autotune(cmb3d_plan_s* p, cudaStream_t s) {
 }
 
 // The FFT passes (draw fused into the first), leaving the real field in buf.
-int run_field(cmb3d_plan_s* p, uint64_t seed, cudaStream_t s) {
+// With `prune` (sky maps of a plan with a pruned transform) the y pass covers
+// only the listed z-planes and stores only the marked rows, and the x pass
+// covers only the listed rows, in the separate-pass shapes of the schedule.
+int run_field(cmb3d_plan_s* p, uint64_t seed, cudaStream_t s, bool prune) {
   if ((p->flags & CMB3D_FLAG_AUTOTUNE) && !p->tuned) {
     int st = autotune(p, s);
     if (st != CMB3D_OK) return st;
@@ -301,6 +315,19 @@ int run_field(cmb3d_plan_s* p, uint64_t seed, cudaStream_t s) {
   e = timed(p, CMB3D_STAGE_DRAW_ZFFT, s,
             [&] { return cmb3d::launch_draw_zfft(p->N, sc.draw, p->buf, p->amp, p->tw, seed, s); });
   if (e != cudaSuccess) return fail_cuda(e, "draw_zfft launch");
+  if (prune && p->prune) {
+    const int yv = sc.y >= 0 ? sc.y : 0, xv = sc.x >= 0 ? sc.x : 0;
+    e = timed(p, CMB3D_STAGE_YFFT, s, [&] {
+      if (yv == gemm_y_variant(p->N)) return launch_y(p, yv, s);
+      return cmb3d::launch_yfft(p->N, yv, p->buf, p->tw, s, p->d_planes, static_cast<int>(p->nplanes),
+                                p->d_rowmask);
+    });
+    if (e != cudaSuccess) return fail_cuda(e, "yfft launch");
+    e = timed(p, CMB3D_STAGE_XC2R, s,
+              [&] { return cmb3d::launch_xc2r(p->N, xv, p->buf, p->tw, s, p->d_rows, p->nrows_pad); });
+    if (e != cudaSuccess) return fail_cuda(e, "xc2r launch");
+    return CMB3D_OK;
+  }
   if (sc.fused >= 0) {
     e = timed(p, CMB3D_STAGE_YX_FUSED, s, [&] { return cmb3d::launch_yx_fused(p->N, sc.fused, p->buf, p->tw, s); });
     if (e != cudaSuccess) return fail_cuda(e, "yx_fused launch");
@@ -359,7 +386,8 @@ int cmb3d_plan(cmb3d_plan_t* out, int N, double L, double r, const double* pix_x
   if (npix > 0 && !pix_xyz) return fail(CMB3D_EINVAL, "pix_xyz is NULL");
   if (interp != CMB3D_TRILINEAR && interp != CMB3D_TRICUBIC) return fail(CMB3D_EINVAL, "interp must be 1 or 3");
   if (flags & ~uint32_t(CMB3D_FLAG_NO_SORT | CMB3D_FLAG_ALLOW_WRAP | CMB3D_FLAG_STAGE_TIMING | CMB3D_FLAG_THREE_PASS |
-                        CMB3D_FLAG_FUSED_YX | CMB3D_FLAG_AUTOTUNE | CMB3D_FLAG_FP16_GEMM))
+                        CMB3D_FLAG_FUSED_YX | CMB3D_FLAG_AUTOTUNE | CMB3D_FLAG_FP16_GEMM |
+                        CMB3D_FLAG_NO_PRUNE))
     return fail(CMB3D_EINVAL, "unknown flag bits");
   if ((flags & CMB3D_FLAG_FP16_GEMM) && (flags & CMB3D_FLAG_FUSED_YX))
     return fail(CMB3D_EINVAL, "CMB3D_FLAG_FP16_GEMM uses separate y and x passes");
@@ -393,6 +421,8 @@ int cmb3d_plan(cmb3d_plan_t* out, int N, double L, double r, const double* pix_x
   // ---- pixel table (FP64 mapping, then FP32 fractions) --------------------
   std::vector<float4> tab;
   std::vector<int32_t> perm;
+  std::vector<uint32_t> rowmask;
+  std::vector<int32_t> planes, rows;
   try {
     tab.resize(static_cast<size_t>(npix));
     std::vector<std::pair<uint64_t, int32_t>> order;
@@ -432,6 +462,55 @@ int cmb3d_plan(cmb3d_plan_t* out, int N, double L, double r, const double* pix_x
     } else {
       tab.swap(raw);
     }
+    // rows (z, y) read by the interpolation stencils: z in bz + OFF .. bz + OFF + K - 1
+    // (mod N), likewise y; consecutive pixels of one row are visited once
+    const int K = interp == CMB3D_TRICUBIC ? 4 : 2, OFF = interp == CMB3D_TRICUBIC ? -1 : 0;
+    const size_t words = static_cast<size_t>(N) * N / 32;
+    if (!(flags & CMB3D_FLAG_NO_PRUNE) && N >= 128 && npix > 0) {
+      rowmask.assign(words, 0u);
+      uint64_t prev = ~uint64_t(0);
+      for (int64_t i = 0; i < npix; ++i) {
+        uint64_t key;
+        if (sort) {
+          key = order[static_cast<size_t>(i)].first / static_cast<uint64_t>(N);
+        } else {
+          uint32_t bits;
+          const float4 e4 = tab[static_cast<size_t>(i)];
+          std::memcpy(&bits, &e4.w, sizeof(bits));
+          uint32_t sgn;
+          std::memcpy(&sgn, &e4.z, sizeof(sgn));
+          const uint64_t by = (bits >> 11) & 2047u, bz = (bits >> 22) | ((sgn >> 31) << 10);
+          key = bz * static_cast<uint64_t>(N) + by;
+        }
+        if (key == prev) continue;
+        prev = key;
+        const int bz = static_cast<int>(key / static_cast<uint64_t>(N)), by = static_cast<int>(key % N);
+        for (int c = 0; c < K; ++c) {
+          const int z = (bz + c + OFF + N) & (N - 1);
+          for (int b = 0; b < K; ++b) {
+            const size_t row = static_cast<size_t>(z) * N + static_cast<size_t>((by + b + OFF + N) & (N - 1));
+            rowmask[row >> 5] |= 1u << (row & 31);
+          }
+        }
+      }
+      for (int z = 0; z < N; ++z) {
+        bool any = false;
+        for (int w = 0; w < N / 32; ++w) {
+          const uint32_t m = rowmask[static_cast<size_t>(z) * (N / 32) + w];
+          any = any || m != 0;
+          for (int bit = 0; bit < 32; ++bit)
+            if ((m >> bit) & 1u) rows.push_back(z * N + w * 32 + bit);
+        }
+        if (any) planes.push_back(z);
+      }
+      if (static_cast<int64_t>(rows.size()) == static_cast<int64_t>(N) * N) {   // nothing to prune
+        rows.clear();
+        planes.clear();
+        rowmask.clear();
+      } else {
+        while (rows.size() % cmb3d::kRowListPad) rows.push_back(N * N);   // scratch row past the box
+      }
+    }
   } catch (const std::bad_alloc&) {
     delete p;
     return fail(CMB3D_ENOMEM, "host allocation of the pixel table");
@@ -444,7 +523,7 @@ int cmb3d_plan(cmb3d_plan_t* out, int N, double L, double r, const double* pix_x
     tw[static_cast<size_t>(m)] = make_float2(static_cast<float>(std::cos(ang)), static_cast<float>(std::sin(ang)));
   }
 
-  const size_t nbuf = static_cast<size_t>(N) * N * (N / 2);
+  const size_t nbuf = static_cast<size_t>(N) * N * (N / 2) + (N / 2);   // + the scratch row
   const size_t nq = 3 * static_cast<size_t>(N / 2) * (N / 2) + 1;
   int st;
   if ((st = dev_alloc(p, &p->buf, nbuf, "box")) != CMB3D_OK ||
@@ -453,7 +532,10 @@ int cmb3d_plan(cmb3d_plan_t* out, int N, double L, double r, const double* pix_x
       (st = dev_alloc(p, &p->tab, static_cast<size_t>(npix), "pixel table")) != CMB3D_OK ||
       (st = dev_alloc(p, &p->outbuf, static_cast<size_t>(npix), "output staging")) != CMB3D_OK ||
       (st = dev_alloc(p, &p->d_err, 1, "error word")) != CMB3D_OK ||
-      (!perm.empty() && (st = dev_alloc(p, &p->perm, perm.size(), "permutation")) != CMB3D_OK)) {
+      (!perm.empty() && (st = dev_alloc(p, &p->perm, perm.size(), "permutation")) != CMB3D_OK) ||
+      (!rows.empty() && ((st = dev_alloc(p, &p->d_rows, rows.size(), "row list")) != CMB3D_OK ||
+                         (st = dev_alloc(p, &p->d_planes, planes.size(), "plane list")) != CMB3D_OK ||
+                         (st = dev_alloc(p, &p->d_rowmask, rowmask.size(), "row mask")) != CMB3D_OK))) {
     free_plan(p);
     return st;
   }
@@ -463,6 +545,18 @@ int cmb3d_plan(cmb3d_plan_t* out, int N, double L, double r, const double* pix_x
     e = cudaMemcpy(p->tab, tab.data(), tab.size() * sizeof(float4), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && !perm.empty())
     e = cudaMemcpy(p->perm, perm.data(), perm.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !rows.empty()) {
+    e = cudaMemcpy(p->d_rows, rows.data(), rows.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(p->d_planes, planes.data(), planes.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(p->d_rowmask, rowmask.data(), rowmask.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    p->prune = true;
+    p->nplanes = static_cast<int64_t>(planes.size());
+    p->nrows_pad = static_cast<int64_t>(rows.size());
+    p->nrows = 0;
+    for (int32_t r : rows) p->nrows += r < N * N ? 1 : 0;
+  }
   if (e != cudaSuccess) {
     free_plan(p);
     return fail_cuda(e, "plan upload");
@@ -586,7 +680,7 @@ int cmb3d_realize_sample(cmb3d_plan_t p, uint64_t seed, float* out_dev, void* st
   if (p->npix > 0 && !out_dev) return fail(CMB3D_EINVAL, "out_dev is NULL");
   DeviceGuard g(p->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if ((st = run_field(p, seed, s)) != CMB3D_OK) return st;
+  if ((st = run_field(p, seed, s, true)) != CMB3D_OK) return st;
   return run_gather(p, out_dev, s);
 }
 
@@ -596,7 +690,7 @@ int cmb3d_realize_sample_to_host(cmb3d_plan_t p, uint64_t seed, float* out_host,
   if (p->npix > 0 && !out_host) return fail(CMB3D_EINVAL, "out_host is NULL");
   DeviceGuard g(p->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if ((st = run_field(p, seed, s)) != CMB3D_OK) return st;
+  if ((st = run_field(p, seed, s, true)) != CMB3D_OK) return st;
   if ((st = run_gather(p, p->outbuf, s)) != CMB3D_OK) return st;
   if (p->npix > 0) {
     cudaError_t e = cudaMemcpyAsync(out_host, p->outbuf, static_cast<size_t>(p->npix) * sizeof(float),
@@ -875,7 +969,7 @@ int cmb3d_realize_field(cmb3d_plan_t p, uint64_t seed, float* field_dev, void* s
   if (!field_dev) return fail(CMB3D_EINVAL, "field_dev is NULL");
   DeviceGuard g(p->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if ((st = run_field(p, seed, s)) != CMB3D_OK) return st;
+  if ((st = run_field(p, seed, s, false)) != CMB3D_OK) return st;
   const size_t bytes = static_cast<size_t>(p->N) * p->N * p->N * sizeof(float);
   cudaError_t e = cudaMemcpyAsync(field_dev, p->buf, bytes, cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return fail_cuda(e, "field copy");
@@ -963,6 +1057,13 @@ int cmb3d_plan_info(cmb3d_plan_t p, int* N, int64_t* npix, int64_t* device_bytes
   if (N) *N = p->N;
   if (npix) *npix = p->npix;
   if (device_bytes) *device_bytes = p->dev_bytes;
+  return CMB3D_OK;
+}
+
+int cmb3d_plan_prune_info(cmb3d_plan_t p, int64_t* planes, int64_t* rows) {
+  if (!p) return fail(CMB3D_EINVAL, "plan is NULL");
+  if (planes) *planes = p->prune ? p->nplanes : p->N;
+  if (rows) *rows = p->prune ? p->nrows : static_cast<int64_t>(p->N) * p->N;
   return CMB3D_OK;
 }
 

@@ -98,7 +98,7 @@ def test_fused_yx_pass_matches_three_pass_and_oracle(N):
     L = 2.2
     kn, pk = smooth_pk(N, L)
     pix = fibonacci_sphere(20000, 4999)
-    flags = cmb3d.CMB3D_FLAG_STAGE_TIMING
+    flags = cmb3d.CMB3D_FLAG_STAGE_TIMING | cmb3d.CMB3D_FLAG_NO_PRUNE     # whole-box passes
     with cmb3d.Plan(N, L, 1.0, pix, 3, flags | cmb3d.CMB3D_FLAG_FUSED_YX) as fused, \
             cmb3d.Plan(N, L, 1.0, pix, 3, flags | cmb3d.CMB3D_FLAG_THREE_PASS) as three:
         fused.set_pk(kn, pk)
@@ -130,7 +130,7 @@ def test_dsmem_fused_pass_matches_three_pass_and_oracle(N):
     kn, pk = smooth_pk(N, L)
     pix = fibonacci_sphere(20000, 7001)
     pb = orc.p_box_of_q(N, L, kn, pk)
-    with cmb3d.Plan(N, L, 1.0, pix, 3, cmb3d.CMB3D_FLAG_STAGE_TIMING) as plan:
+    with cmb3d.Plan(N, L, 1.0, pix, 3, cmb3d.CMB3D_FLAG_STAGE_TIMING | cmb3d.CMB3D_FLAG_NO_PRUNE) as plan:
         plan.set_pk(kn, pk)
         cmb3d.cmb3d_plan_set_schedule(plan.handle, (0, -1, -1, 2))
         a = plan.realize_sample(11).cpu().numpy()
@@ -155,7 +155,7 @@ def test_every_kernel_variant_matches_oracle(N):
     ref = orc.realize_sample(N, L, 1.0, pix, orc.p_box_of_q(N, L, kn, pk), 17, 3)
     scheds = [(d, 0, 0, -1) for d in range(3)] + [(0, y, 0, -1) for y in range(3)] + \
              [(0, 0, x, -1) for x in range(3)] + [(0, -1, -1, f) for f in range(3)]
-    with cmb3d.Plan(N, L, 1.0, pix, 3) as plan:
+    with cmb3d.Plan(N, L, 1.0, pix, 3, cmb3d.CMB3D_FLAG_NO_PRUNE) as plan:
         plan.set_pk(kn, pk)
         for sc in scheds:
             cmb3d.cmb3d_plan_set_schedule(plan.handle, sc)
