@@ -130,28 +130,49 @@ def source_hash(files):
     return h.hexdigest()[:16]
 
 
+_FFT_SRC = ["paper_2507_15703_gb300/csrc/fft_passes.cu", "paper_2507_15703_gb300/csrc/fft_tiles.cuh",
+            "paper_2507_15703_gb300/csrc/device_common.cuh"]
 KERNEL_SOURCES = {
-    "draw_zfft": ["paper_2507_15703_gb300/csrc/fft_passes.cu", "paper_2507_15703_gb300/csrc/device_common.cuh"],
-    "yfft": ["paper_2507_15703_gb300/csrc/fft_passes.cu", "paper_2507_15703_gb300/csrc/device_common.cuh"],
-    "xc2r": ["paper_2507_15703_gb300/csrc/fft_passes.cu", "paper_2507_15703_gb300/csrc/device_common.cuh"],
-    "gather": ["paper_2507_15703_gb300/csrc/gather.cu"],
-    "yx_fused": ["paper_2507_15703_gb300/csrc/fft_passes.cu", "paper_2507_15703_gb300/csrc/device_common.cuh"],
+    "draw_zfft": _FFT_SRC,
+    "yfft": _FFT_SRC,
+    "xc2r": _FFT_SRC,
+    "yx_fused": _FFT_SRC,
+    "gather": ["paper_2507_15703_gb300/csrc/gather.cu", "paper_2507_15703_gb300/csrc/gather_tiles.cuh"],
     "batch": ["paper_2507_15703_gb300/csrc/batch.cu", "paper_2507_15703_gb300/csrc/fft_tiles.cuh"],
 }
+# kernels whose limiter is instruction issue, not HBM (the draw: Philox,
+# Box-Muller and the first FFT stages for every mode, one write of the box)
+ALU_BOUND = {"draw_zfft"}
 
 
-def ncu_traffic(kernel: str, workload: str):
-    """DRAM bytes per launch from the committed ncu summary, or None when the
-    kernel source changed since the counters were taken."""
+def ncu_counters(kernel: str, workload: str):
+    """Per-launch counters of the kernel from the committed ncu summary
+    (dram_bytes_per_launch, thread_inst_per_launch), or None when the kernel
+    source changed since they were taken."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
-    if not os.path.exists(p):
+    if not os.path.exists(p) or kernel not in KERNEL_SOURCES:
         return None
     with open(p) as f:
         d = json.load(f)
     e = d.get(workload, {}).get(kernel)
     if not e or e.get("source_hash") != source_hash(KERNEL_SOURCES[kernel]):
         return None
-    return e.get("dram_bytes_per_launch")
+    return e
+
+
+def ncu_traffic(kernel: str, workload: str):
+    e = ncu_counters(kernel, workload)
+    return e.get("dram_bytes_per_launch") if e else None
+
+
+def alu_peak_tinst(clk) -> tuple[float, str]:
+    """Lane-instructions per second at full issue: SMs x 4 schedulers x 32
+    lanes x the maximum SM clock (one warp instruction per scheduler per
+    clock), in units of 1e12."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = (clk or {}).get("sm_max_mhz") or 2070.0
+    return sms * 128 * mhz * 1e6 / 1e12, f"derived: {sms} SMs x 4 schedulers x 32 lanes x {mhz:.0f} MHz"
 
 
 def algorithmic_bytes(N: int, npix: int, planes: int | None = None, rows: int | None = None) -> dict:
@@ -196,6 +217,8 @@ def run_cuda(args, rank, world, local):
         flags |= cmb3d.CMB3D_FLAG_FP16_GEMM
     if args.no_prune:
         flags |= cmb3d.CMB3D_FLAG_NO_PRUNE
+    if args.pipeline:
+        flags |= cmb3d.CMB3D_FLAG_PIPELINE
     if args.schedule:
         flags &= ~cmb3d.CMB3D_FLAG_AUTOTUNE
     plan = cmb3d.Plan(w.N, w.L, w.r, pix, w.interp, flags)
@@ -206,6 +229,8 @@ def run_cuda(args, rank, world, local):
         fit_err = learned["summary"]["mlp_fwd_err_rms_median"]
     else:
         fit_err = plan.set_cl(ell, cl, w.nkbins)
+        kn_fit = np.linspace(0.0, math.sqrt(3) * math.pi * w.N / w.L, w.nkbins)   # the fit's nodes
+        plan_pk = (kn_fit, cmb3d.cmb3d_get_pk(plan.handle, kn_fit))
     setup_s = time.time() - t0
     stream = torch.cuda.current_stream(dev)
     out = torch.empty(npix, dtype=torch.float32, device=dev)
@@ -262,6 +287,28 @@ def run_cuda(args, rank, world, local):
     torch.cuda.synchronize(dev)
     d2h_ms = ev0.elapsed_time(ev1) / args.steps
     cmb3d.cmb3d_stage_times(plan.handle, reset=True)
+    pipe_info = None
+    if not args.pipeline and learned is None:
+        # the same maps through a pipelined plan (second box, draw of map i+1
+        # overlapping the passes and gather of map i); CUDA events, same stream
+        pflags = (flags | cmb3d.CMB3D_FLAG_PIPELINE) & ~cmb3d.CMB3D_FLAG_STAGE_TIMING & ~cmb3d.CMB3D_FLAG_AUTOTUNE
+        pplan = cmb3d.Plan(w.N, w.L, w.r, pix, w.interp, pflags)
+        cmb3d.cmb3d_plan_set_schedule(pplan.handle, schedule)
+        pplan.set_pk(*plan_pk)
+        for i in range(args.warmup):
+            pplan.realize_sample(seed0 + i, out, stream)
+        barrier()
+        ev0.record(stream)
+        for i in range(args.steps):
+            pplan.realize_sample(seed0 + args.warmup + i, out, stream)
+        ev1.record(stream)
+        barrier()
+        p_ms = max_over_ranks(dist, ev0.elapsed_time(ev1), dev)
+        pplan.close()
+        pipe_info = {"maps_per_s": round(world * args.steps / (p_ms / 1e3), 3),
+                     "ms_per_map": round(p_ms / args.steps, 5),
+                     "note": "CMB3D_FLAG_PIPELINE: two boxes, each map's draw overlaps the previous map's "
+                             "passes and gather (timed after the main run, same maps and stream)"}
     plan.close()
 
     if rank != 0:
@@ -285,12 +332,14 @@ def run_cuda(args, rank, world, local):
               "parallelism": f"replicas x{world}",
               "schedule": {"draw": schedule[0], "y": schedule[1], "x": schedule[2], "fused_yx": schedule[3],
                            "restriction": "three-pass" if args.three_pass else "fused" if args.fused else "autotuned",
-                           "y_pass": "split-FP16 DFT-GEMM (tcgen05)" if args.fp16_gemm else "FP32 butterflies"},
+                           "y_pass": "split-FP16 DFT-GEMM (tcgen05)" if args.fp16_gemm else "FP32 butterflies",
+                           "pipelined": bool(args.pipeline)},
               "pruned_transform": {"z_planes": n_planes, "rows": n_rows, "of_planes": w.N, "of_rows": w.N ** 2,
                                    "note": "y pass on the z-planes, x pass on the (z, y) rows the "
                                            "interpolation stencils read; maps equal the whole-box maps bit for bit"},
               "l2": f"no flush: per-map working set {per_map_bytes / 2**30:.2f} GiB > 129 MiB L2",
               "cl_fit_max_rel_err": fit_err, "plan_setup_s": round(setup_s, 2),
+              "pipelined_plan": pipe_info,
               "e2e_d2h_ms_per_map": round(d2h_ms, 4),
               "e2e_d2h_gbs": round(4 * npix / (d2h_ms / 1e3) / 1e9, 1)}
     if learned is not None:
@@ -444,6 +493,9 @@ def run_cuda_batch(args, rank, world, local, w):
             h.copy_(o, non_blocking=True)
         torch.cuda.synchronize(dev)
     e2e_s = max_over_ranks(dist, time.perf_counter() - t1, dev)
+    # the two-stream form runs each box's pruned transform, the persistent kernel the whole box
+    pruned = form == 1
+    extents = [cmb3d.cmb3d_plan_prune_info(p.handle) if pruned else (w.N, w.N ** 2) for p in plans]
     for p in plans:
         p.close()
     if rank != 0:
@@ -451,8 +503,10 @@ def run_cuda_batch(args, rank, world, local, w):
         return
     maps = world * args.steps * w.batch
     value = maps / (t_max / 1e3)
-    ab = algorithmic_bytes(w.N, 0)
-    batch_bytes = w.batch * (ab["draw_zfft"] + ab["yfft"] + ab["xc2r"]) + 24 * sum(npix)
+    batch_bytes = 24 * sum(npix)
+    for zp, rw in extents:
+        ab = algorithmic_bytes(w.N, 0, zp, rw)
+        batch_bytes += ab["draw_zfft"] + ab["yfft"] + ab["xc2r"]
     kernels = {"batch": kernel_entry(args.steps, ms, ms, batch_bytes)}
     kernels["batch"]["note"] = "one step = the whole batch (persistent kernel or graph), CUDA events"
     config = {"workload": args.workload, "N": w.N, "boxes_per_step": w.batch, "npix_total": int(sum(npix)),
@@ -461,6 +515,9 @@ def run_cuda_batch(args, rank, world, local, w):
               "parallelism": f"replicas x{world}", "schedule": f"autotuned: {form_name}",
               "l2": f"no flush: per-step working set {batch_bytes / 2**30:.1f} GiB > 129 MiB L2",
               "cl_fit_max_rel_err": fit_err, "plan_setup_s": round(setup_s, 2),
+              "pruned_transform": {"z_planes_mean": round(float(np.mean([e[0] for e in extents])), 1),
+                                   "rows_mean": round(float(np.mean([e[1] for e in extents])), 1),
+                                   "of_planes": w.N, "of_rows": w.N ** 2},
               "plain_form_maps_per_s": round(plain_value, 1)}
     emit(args, w, value, t_max, world, config, batch_bytes / w.batch, kernels, "batch", maps / e2e_s,
          4 * sum(npix), 2 * args.steps, clk)
@@ -497,6 +554,25 @@ def kernel_entry(n, total_ms, all_ms, alg_bytes):
             "alg_bytes": int(alg_bytes), "alg_gbs": round(gbs, 1), "frac_of_measured_hbm": round(gbs / peak, 4)}
 
 
+def roofline(dom, dk, workload, peak, peak_kind, clk):
+    """Roofline of the dominant kernel.  HBM-bound kernels: algorithmic bytes
+    per launch / CUDA-event time against the measured copy bandwidth.  The
+    issue-bound draw: its executed lane-instructions per launch (a fixed
+    property of the compiled kernel and N, from the committed ncu counters) /
+    CUDA-event time against full issue; falls back to HBM if the counters are
+    stale."""
+    cnt = ncu_counters(dom, workload)
+    if dom in ALU_BOUND and cnt and cnt.get("thread_inst_per_launch"):
+        p, src = alu_peak_tinst(clk)
+        a = cnt["thread_inst_per_launch"] / (dk["avg_ms"] / 1e3) / 1e12
+        return {"bound": "alu", "kernel": dom, "achieved": round(a, 2), "peak": round(p, 2), "unit": "Tinst/s",
+                "frac": round(a / p, 4), "peak_source": src, "traffic": cnt.get("dram_bytes_per_launch"),
+                "inst_per_launch": cnt["thread_inst_per_launch"], "hbm_frac": dk["frac_of_measured_hbm"]}
+    return {"bound": "hbm", "kernel": dom, "achieved": dk["alg_gbs"], "peak": peak, "unit": "GB/s",
+            "frac": dk["frac_of_measured_hbm"], "peak_source": peak_kind,
+            "traffic": cnt.get("dram_bytes_per_launch") if cnt else None}
+
+
 def emit(args, w, value, t_max, world, config, per_map_bytes, kernels, dom, e2e_value, d2h_bytes, launches, clk):
     peak, peak_kind = measured_peaks()
     dk = kernels[dom]
@@ -515,9 +591,7 @@ def emit(args, w, value, t_max, world, config, per_map_bytes, kernels, dom, e2e_
         "data": "synthetic: Fibonacci-grid polar cap pixels, C_l family inverted to P(k) by the library's NNLS",
         "config": config,
         "achieved_gbs_alg_per_map": round(per_map_bytes * value / world / 1e9, 1),
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": dk["alg_gbs"], "peak": peak, "unit": "GB/s",
-                     "frac": dk["frac_of_measured_hbm"], "peak_source": peak_kind,
-                     "traffic": ncu_traffic(dom, args.workload)},
+        "roofline": roofline(dom, dk, args.workload, peak, peak_kind, clk),
         "kernels": kernels,
         "e2e": {"value": round(e2e_value, 3), "unit": "maps/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": int(d2h_bytes)},
@@ -621,6 +695,9 @@ def main():
     ap.add_argument("--three-pass", action="store_true", help="only separate y and x passes")
     ap.add_argument("--fused", action="store_true", help="only the fused y+x pass")
     ap.add_argument("--no-prune", action="store_true", help="transform the whole box for every map")
+    ap.add_argument("--pipeline", action="store_true",
+                    help="time the pipelined plan (two boxes, each map's draw overlapping the previous map's "
+                         "passes and gather); by default it is timed after the main run and reported in config")
     ap.add_argument("--sweep", action="store_true", help="also time every kernel variant (stderr)")
     ap.add_argument("--schedule", default="",
                     help="fixed kernel variants 'draw,y,x,fused' (fused -1: separate passes) instead of the autotuner")

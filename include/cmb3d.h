@@ -77,11 +77,18 @@ enum {
                                          (hi+lo) DFT-GEMMs on the tensor cores, FP32
                                          accumulation (N = 256, 512, 1024; else
                                          CMB3D_EUNSUPPORTED); tolerance 1e-3 of rms    */
-  CMB3D_FLAG_NO_PRUNE = 1u << 7       /* sky maps transform the whole box: by default
+  CMB3D_FLAG_NO_PRUNE = 1u << 7,      /* sky maps transform the whole box: by default
                                          (N >= 128) the y pass covers only the z-planes
                                          and stores only the (z, y) rows, and the x pass
                                          only the rows, that the pixels' interpolation
                                          stencils read; the maps are identical          */
+  CMB3D_FLAG_PIPELINE = 1u << 8       /* a second box (4 N^3 more bytes) and two
+                                         internal streams: the draw of a sky map
+                                         overlaps the passes and gather of the previous
+                                         map of the plan.  Stream semantics are kept:
+                                         the map's kernels run after the caller's stream
+                                         at the call, and the caller's stream waits for
+                                         the map.  Maps are identical                   */
 };
 
 /* Spectrum kinds for cmb3d_set_spectrum. */

@@ -122,6 +122,15 @@ struct cmb3d_plan_s {
   int32_t* d_planes = nullptr;
   int32_t* d_rows = nullptr;
   uint32_t* d_rowmask = nullptr;   // N bits per z-plane
+  // CMB3D_FLAG_PIPELINE: a second box and two internal streams; the draw of a
+  // map (dstream) overlaps the passes and gather of the previous map (pstream,
+  // higher priority).  ev_free[k]: box k's last gather done; ev_call: the
+  // caller's stream at the call.
+  bool pipe = false;
+  float2* buf2 = nullptr;
+  cudaStream_t dstream = nullptr, pstream = nullptr;
+  cudaEvent_t ev_drawn[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr}, ev_call = nullptr;
+  int next_box = 0;
 };
 
 namespace {
@@ -155,6 +164,13 @@ int dev_alloc(cmb3d_plan_s* p, T** ptr, size_t count, const char* what) {
 void free_plan(cmb3d_plan_s* p) {
   if (!p) return;
   DeviceGuard g(p->device);
+  if (p->dstream) cudaStreamSynchronize(p->dstream);
+  if (p->pstream) cudaStreamSynchronize(p->pstream);
+  for (cudaEvent_t ev : {p->ev_drawn[0], p->ev_drawn[1], p->ev_free[0], p->ev_free[1], p->ev_call})
+    if (ev) cudaEventDestroy(ev);
+  if (p->dstream) cudaStreamDestroy(p->dstream);
+  if (p->pstream) cudaStreamDestroy(p->pstream);
+  cudaFree(p->buf2);
   p->batch.release();
   cudaFree(p->buf);
   cudaFree(p->amp);
@@ -180,9 +196,34 @@ bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 int num_y_variants(int N) { return cmb3d::num_col_variants(N) + (cmb3d::yfft_gemm_supported(N) ? 1 : 0); }
 int gemm_y_variant(int N) { return cmb3d::yfft_gemm_supported(N) ? cmb3d::num_col_variants(N) : -1; }
 
-cudaError_t launch_y(cmb3d_plan_s* p, int v, cudaStream_t s) {
-  if (v == gemm_y_variant(p->N)) return cmb3d::launch_yfft_gemm(p->N, p->buf, p->tw, p->d_err, s);
-  return cmb3d::launch_yfft(p->N, v, p->buf, p->tw, s);
+cudaError_t launch_y(cmb3d_plan_s* p, int v, cudaStream_t s, float2* box = nullptr) {
+  if (!box) box = p->buf;
+  if (v == gemm_y_variant(p->N)) return cmb3d::launch_yfft_gemm(p->N, box, p->tw, p->d_err, s);
+  return cmb3d::launch_yfft(p->N, v, box, p->tw, s);
+}
+
+// Make stream s wait for everything the plan's internal streams have queued
+// (pipelined plans), before work on s that uses the plan's boxes.
+cudaError_t join_pipeline(cmb3d_plan_s* p, cudaStream_t s) {
+  if (!p->pipe) return cudaSuccess;
+  cudaError_t e = cudaStreamWaitEvent(s, p->ev_free[0], 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->ev_free[1], 0);
+  return e;
+}
+
+// After work on stream s that used box 0 outside the pipeline: the next
+// pipelined draw into box 0 waits for it.
+cudaError_t mark_box0_used(cmb3d_plan_s* p, cudaStream_t s) {
+  return p->pipe ? cudaEventRecord(p->ev_free[0], s) : cudaSuccess;
+}
+
+// Wait on the host for the plan's internal streams (before host-side updates
+// of device tables they read).
+cudaError_t drain_pipeline(cmb3d_plan_s* p) {
+  if (!p->pipe) return cudaSuccess;
+  cudaError_t e = cudaStreamSynchronize(p->dstream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->pstream);
+  return e;
 }
 
 // Error word of the plan's kernels (synchronises); CMB3D_ETIMEOUT if set.
@@ -301,51 +342,98 @@ int autotune(cmb3d_plan_s* p, cudaStream_t s) {
   return CMB3D_OK;
 }
 
-// The FFT passes (draw fused into the first), leaving the real field in buf.
-// With `prune` (sky maps of a plan with a pruned transform) the y pass covers
-// only the listed z-planes and stores only the marked rows, and the x pass
-// covers only the listed rows, in the separate-pass shapes of the schedule.
-int run_field(cmb3d_plan_s* p, uint64_t seed, cudaStream_t s, bool prune) {
-  if ((p->flags & CMB3D_FLAG_AUTOTUNE) && !p->tuned) {
-    int st = autotune(p, s);
-    if (st != CMB3D_OK) return st;
-  }
+int ensure_tuned(cmb3d_plan_s* p, cudaStream_t s) {
+  if (!(p->flags & CMB3D_FLAG_AUTOTUNE) || p->tuned) return CMB3D_OK;
+  if (cudaError_t e = join_pipeline(p, s); e != cudaSuccess) return fail_cuda(e, "pipeline join");
+  return autotune(p, s);
+}
+
+// Draw fused with the z pass into `box`.
+int run_draw(cmb3d_plan_s* p, uint64_t seed, cudaStream_t s, float2* box) {
+  const Schedule& sc = p->sched;
+  cudaError_t e = timed(p, CMB3D_STAGE_DRAW_ZFFT, s,
+                        [&] { return cmb3d::launch_draw_zfft(p->N, sc.draw, box, p->amp, p->tw, seed, s); });
+  if (e != cudaSuccess) return fail_cuda(e, "draw_zfft launch");
+  return CMB3D_OK;
+}
+
+// The y and x passes on `box`, leaving the real field.  With `prune` (sky maps
+// of a plan with a pruned transform) the y pass covers only the listed
+// z-planes and stores only the marked rows, and the x pass covers only the
+// listed rows, in the separate-pass shapes of the schedule.
+int run_passes(cmb3d_plan_s* p, cudaStream_t s, bool prune, float2* box) {
   const Schedule& sc = p->sched;
   cudaError_t e;
-  e = timed(p, CMB3D_STAGE_DRAW_ZFFT, s,
-            [&] { return cmb3d::launch_draw_zfft(p->N, sc.draw, p->buf, p->amp, p->tw, seed, s); });
-  if (e != cudaSuccess) return fail_cuda(e, "draw_zfft launch");
   if (prune && p->prune) {
     const int yv = sc.y >= 0 ? sc.y : 0, xv = sc.x >= 0 ? sc.x : 0;
     e = timed(p, CMB3D_STAGE_YFFT, s, [&] {
-      if (yv == gemm_y_variant(p->N)) return launch_y(p, yv, s);
-      return cmb3d::launch_yfft(p->N, yv, p->buf, p->tw, s, p->d_planes, static_cast<int>(p->nplanes),
-                                p->d_rowmask);
+      if (yv == gemm_y_variant(p->N)) return launch_y(p, yv, s, box);
+      return cmb3d::launch_yfft(p->N, yv, box, p->tw, s, p->d_planes, static_cast<int>(p->nplanes), p->d_rowmask);
     });
     if (e != cudaSuccess) return fail_cuda(e, "yfft launch");
     e = timed(p, CMB3D_STAGE_XC2R, s,
-              [&] { return cmb3d::launch_xc2r(p->N, xv, p->buf, p->tw, s, p->d_rows, p->nrows_pad); });
+              [&] { return cmb3d::launch_xc2r(p->N, xv, box, p->tw, s, p->d_rows, p->nrows_pad); });
     if (e != cudaSuccess) return fail_cuda(e, "xc2r launch");
     return CMB3D_OK;
   }
   if (sc.fused >= 0) {
-    e = timed(p, CMB3D_STAGE_YX_FUSED, s, [&] { return cmb3d::launch_yx_fused(p->N, sc.fused, p->buf, p->tw, s); });
+    e = timed(p, CMB3D_STAGE_YX_FUSED, s, [&] { return cmb3d::launch_yx_fused(p->N, sc.fused, box, p->tw, s); });
     if (e != cudaSuccess) return fail_cuda(e, "yx_fused launch");
     return CMB3D_OK;
   }
-  e = timed(p, CMB3D_STAGE_YFFT, s, [&] { return launch_y(p, sc.y, s); });
+  e = timed(p, CMB3D_STAGE_YFFT, s, [&] { return launch_y(p, sc.y, s, box); });
   if (e != cudaSuccess) return fail_cuda(e, "yfft launch");
-  e = timed(p, CMB3D_STAGE_XC2R, s, [&] { return cmb3d::launch_xc2r(p->N, sc.x, p->buf, p->tw, s); });
+  e = timed(p, CMB3D_STAGE_XC2R, s, [&] { return cmb3d::launch_xc2r(p->N, sc.x, box, p->tw, s); });
   if (e != cudaSuccess) return fail_cuda(e, "xc2r launch");
   return CMB3D_OK;
 }
 
-int run_gather(cmb3d_plan_s* p, float* out, cudaStream_t s) {
+// The whole realization into p->buf on stream s (after the pipeline, if any).
+int run_field(cmb3d_plan_s* p, uint64_t seed, cudaStream_t s, bool prune) {
+  int st = ensure_tuned(p, s);
+  if (st != CMB3D_OK) return st;
+  if (cudaError_t e = join_pipeline(p, s); e != cudaSuccess) return fail_cuda(e, "pipeline join");
+  if ((st = run_draw(p, seed, s, p->buf)) != CMB3D_OK) return st;
+  return run_passes(p, s, prune, p->buf);
+}
+
+int run_gather(cmb3d_plan_s* p, float* out, cudaStream_t s, const float2* box = nullptr) {
+  const float* field = reinterpret_cast<const float*>(box ? box : p->buf);
   cudaError_t e = timed(p, CMB3D_STAGE_GATHER, s, [&] {
-    return cmb3d::launch_gather(p->N, p->interp, reinterpret_cast<const float*>(p->buf), p->tab, p->perm, out,
-                                p->npix, s);
+    return cmb3d::launch_gather(p->N, p->interp, field, p->tab, p->perm, out, p->npix, s);
   });
   if (e != cudaSuccess) return fail_cuda(e, "gather launch");
+  return CMB3D_OK;
+}
+
+// One sky map into `out` through the pipelined plan: the draw on dstream into
+// the next box once that box's previous gather is done, the passes and the
+// gather on pstream after the draw and after the caller's stream at the call,
+// and the caller's stream after the gather.
+int run_map_pipelined(cmb3d_plan_s* p, uint64_t seed, float* out, cudaStream_t s) {
+  const bool was_tuned = p->tuned;
+  int st = ensure_tuned(p, s);
+  if (st != CMB3D_OK) return st;
+  if (p->tuned != was_tuned) {                        // the autotuner just used box 0 on s
+    cudaError_t e = cudaEventRecord(p->ev_free[0], s);
+    if (e != cudaSuccess) return fail_cuda(e, "pipeline order");
+  }
+  const int k = p->next_box;
+  float2* box = k ? p->buf2 : p->buf;
+  cudaError_t e = cudaStreamWaitEvent(p->dstream, p->ev_free[k], 0);
+  if (e != cudaSuccess) return fail_cuda(e, "pipeline wait");
+  if ((st = run_draw(p, seed, p->dstream, box)) != CMB3D_OK) return st;
+  e = cudaEventRecord(p->ev_drawn[k], p->dstream);
+  if (e == cudaSuccess) e = cudaEventRecord(p->ev_call, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(p->pstream, p->ev_call, 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(p->pstream, p->ev_drawn[k], 0);
+  if (e != cudaSuccess) return fail_cuda(e, "pipeline order");
+  if ((st = run_passes(p, p->pstream, true, box)) != CMB3D_OK) return st;
+  if ((st = run_gather(p, out, p->pstream, box)) != CMB3D_OK) return st;
+  e = cudaEventRecord(p->ev_free[k], p->pstream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->ev_free[k], 0);
+  if (e != cudaSuccess) return fail_cuda(e, "pipeline order");
+  p->next_box = k ^ 1;
   return CMB3D_OK;
 }
 
@@ -387,7 +475,7 @@ int cmb3d_plan(cmb3d_plan_t* out, int N, double L, double r, const double* pix_x
   if (interp != CMB3D_TRILINEAR && interp != CMB3D_TRICUBIC) return fail(CMB3D_EINVAL, "interp must be 1 or 3");
   if (flags & ~uint32_t(CMB3D_FLAG_NO_SORT | CMB3D_FLAG_ALLOW_WRAP | CMB3D_FLAG_STAGE_TIMING | CMB3D_FLAG_THREE_PASS |
                         CMB3D_FLAG_FUSED_YX | CMB3D_FLAG_AUTOTUNE | CMB3D_FLAG_FP16_GEMM |
-                        CMB3D_FLAG_NO_PRUNE))
+                        CMB3D_FLAG_NO_PRUNE | CMB3D_FLAG_PIPELINE))
     return fail(CMB3D_EINVAL, "unknown flag bits");
   if ((flags & CMB3D_FLAG_FP16_GEMM) && (flags & CMB3D_FLAG_FUSED_YX))
     return fail(CMB3D_EINVAL, "CMB3D_FLAG_FP16_GEMM uses separate y and x passes");
@@ -557,6 +645,19 @@ int cmb3d_plan(cmb3d_plan_t* out, int N, double L, double r, const double* pix_x
     p->nrows = 0;
     for (int32_t r : rows) p->nrows += r < N * N ? 1 : 0;
   }
+  if (e == cudaSuccess && (flags & CMB3D_FLAG_PIPELINE)) {
+    if ((st = dev_alloc(p, &p->buf2, nbuf, "second box")) != CMB3D_OK) {
+      free_plan(p);
+      return st;
+    }
+    int lo = 0, hi = 0;
+    e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->dstream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&p->pstream, cudaStreamNonBlocking, hi);
+    for (cudaEvent_t* ev : {&p->ev_drawn[0], &p->ev_drawn[1], &p->ev_free[0], &p->ev_free[1], &p->ev_call})
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    p->pipe = e == cudaSuccess;
+  }
   if (e != cudaSuccess) {
     free_plan(p);
     return fail_cuda(e, "plan upload");
@@ -657,7 +758,8 @@ int cmb3d_set_spectrum(cmb3d_plan_t p, int kind, const double* x, const double* 
     amp[q] = static_cast<float>(std::sqrt(pb / 2.0));
   }
   DeviceGuard g(p->device);
-  cudaError_t e = cudaMemcpy(p->amp, amp.data(), nq * sizeof(float), cudaMemcpyHostToDevice);
+  cudaError_t e = drain_pipeline(p);                 // no draw of the plan still reads amp
+  if (e == cudaSuccess) e = cudaMemcpy(p->amp, amp.data(), nq * sizeof(float), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return fail_cuda(e, "amplitude upload");
   p->knodes.swap(kn);
   p->pnodes.swap(pn);
@@ -680,6 +782,7 @@ int cmb3d_realize_sample(cmb3d_plan_t p, uint64_t seed, float* out_dev, void* st
   if (p->npix > 0 && !out_dev) return fail(CMB3D_EINVAL, "out_dev is NULL");
   DeviceGuard g(p->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (p->pipe) return run_map_pipelined(p, seed, out_dev, s);
   if ((st = run_field(p, seed, s, true)) != CMB3D_OK) return st;
   return run_gather(p, out_dev, s);
 }
@@ -690,8 +793,12 @@ int cmb3d_realize_sample_to_host(cmb3d_plan_t p, uint64_t seed, float* out_host,
   if (p->npix > 0 && !out_host) return fail(CMB3D_EINVAL, "out_host is NULL");
   DeviceGuard g(p->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if ((st = run_field(p, seed, s, true)) != CMB3D_OK) return st;
-  if ((st = run_gather(p, p->outbuf, s)) != CMB3D_OK) return st;
+  if (p->pipe) {
+    if ((st = run_map_pipelined(p, seed, p->outbuf, s)) != CMB3D_OK) return st;
+  } else {
+    if ((st = run_field(p, seed, s, true)) != CMB3D_OK) return st;
+    if ((st = run_gather(p, p->outbuf, s)) != CMB3D_OK) return st;
+  }
   if (p->npix > 0) {
     cudaError_t e = cudaMemcpyAsync(out_host, p->outbuf, static_cast<size_t>(p->npix) * sizeof(float),
                                     cudaMemcpyDeviceToHost, s);
@@ -819,7 +926,13 @@ int batch_streams(const cmb3d_plan_t* plans, const uint64_t* seeds, float* const
         if (el == cudaSuccess) el = cudaEventRecord(ev[static_cast<size_t>(b)], bc.cap);
         if (el == cudaSuccess) el = cudaStreamWaitEvent(bc.cap2, ev[static_cast<size_t>(b)], 0);
         if (el == cudaSuccess) {
-          if (sc.fused >= 0) {
+          if (p->prune) {                         // the box's pruned transform (run_field)
+            const int yv = sc.y >= 0 ? sc.y : 0, xv = sc.x >= 0 ? sc.x : 0;
+            el = yv == gemm_y_variant(N) ? launch_y(p, yv, bc.cap2)
+                                         : cmb3d::launch_yfft(N, yv, p->buf, p->tw, bc.cap2, p->d_planes,
+                                                              static_cast<int>(p->nplanes), p->d_rowmask);
+            if (el == cudaSuccess) el = cmb3d::launch_xc2r(N, xv, p->buf, p->tw, bc.cap2, p->d_rows, p->nrows_pad);
+          } else if (sc.fused >= 0) {
             el = cmb3d::launch_yx_fused(N, sc.fused, p->buf, p->tw, bc.cap2);
           } else {
             el = cmb3d::launch_yfft(N, sc.y, p->buf, p->tw, bc.cap2);
@@ -938,7 +1051,14 @@ int cmb3d_realize_sample_batch(const cmb3d_plan_t* plans, const uint64_t* seeds,
   }
   DeviceGuard g(plans[0]->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (cmb3d::batch_supported(plans[0]->N)) return batch_run(plans, seeds, outs_dev, B, s);
+  if (cmb3d::batch_supported(plans[0]->N)) {
+    for (int b = 0; b < B; ++b)
+      if (cudaError_t e = join_pipeline(plans[b], s); e != cudaSuccess) return fail_cuda(e, "pipeline join");
+    int st = batch_run(plans, seeds, outs_dev, B, s);
+    for (int b = 0; b < B && st == CMB3D_OK; ++b)
+      if (cudaError_t e = mark_box0_used(plans[b], s); e != cudaSuccess) return fail_cuda(e, "pipeline order");
+    return st;
+  }
   for (int b = 0; b < B; ++b) {
     int st = cmb3d_realize_sample(plans[b], seeds[b], outs_dev[b], stream);
     if (st != CMB3D_OK) return st;
@@ -972,6 +1092,7 @@ int cmb3d_realize_field(cmb3d_plan_t p, uint64_t seed, float* field_dev, void* s
   if ((st = run_field(p, seed, s, false)) != CMB3D_OK) return st;
   const size_t bytes = static_cast<size_t>(p->N) * p->N * p->N * sizeof(float);
   cudaError_t e = cudaMemcpyAsync(field_dev, p->buf, bytes, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = mark_box0_used(p, s);
   if (e != cudaSuccess) return fail_cuda(e, "field copy");
   return CMB3D_OK;
 }

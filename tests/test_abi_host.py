@@ -58,7 +58,7 @@ def test_plan_rejects_unsupported_sizes(lib, N):
     assert e.value.status == cmb3d.CMB3D_EUNSUPPORTED
 
 
-@pytest.mark.parametrize("kw", [dict(L=1.5), dict(L=-1.0), dict(r=0.0), dict(interp=2), dict(flags=1 << 8),
+@pytest.mark.parametrize("kw", [dict(L=1.5), dict(L=-1.0), dict(r=0.0), dict(interp=2), dict(flags=1 << 9),
                                 dict(L=float("nan"))])
 def test_plan_rejects_bad_arguments(lib, kw):
     args = dict(N=64, L=2.2, r=1.0, interp=1, flags=0)

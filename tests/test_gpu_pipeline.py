@@ -1,0 +1,120 @@
+"""Pipelined plans (CMB3D_FLAG_PIPELINE): two boxes and two internal streams,
+the draw of a map overlapping the passes and gather of the previous one.
+
+Every map must equal the map of a plain plan bit for bit (same kernels, same
+arithmetic), whatever is interleaved: maps issued back to back without a
+synchronisation, the whole field, a new spectrum, the host-output entry
+point, the autotuner on the first call, and batches.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2507_15703_gb300 import cmb3d  # noqa: E402
+from synth import cap_pixels  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    cmb3d.load()
+
+
+def smooth_pk(N, L, nk=96, amp=1e-3):
+    k = np.linspace(0.0, np.sqrt(3) * np.pi * N / L, nk)
+    return k, amp / (1.0 + (k / 12.0) ** 3)
+
+
+@pytest.mark.parametrize("N,flags", [(128, 0), (256, cmb3d.CMB3D_FLAG_STAGE_TIMING), (256, cmb3d.CMB3D_FLAG_NO_PRUNE)])
+def test_back_to_back_maps_equal_plain_maps(N, flags):
+    L = 2.2
+    kn, pk = smooth_pk(N, L)
+    pix = cap_pixels(128, 0.3)
+    seeds = list(range(100, 109))
+    with cmb3d.Plan(N, L, 1.0, pix, 3, flags | cmb3d.CMB3D_FLAG_PIPELINE) as piped, \
+            cmb3d.Plan(N, L, 1.0, pix, 3, flags) as plain:
+        piped.set_pk(kn, pk)
+        plain.set_pk(kn, pk)
+        outs = [torch.empty(len(pix), dtype=torch.float32, device="cuda") for _ in seeds]
+        for sd, o in zip(seeds, outs):                       # no synchronisation in between
+            piped.realize_sample(sd, o)
+        torch.cuda.synchronize()
+        for sd, o in zip(seeds, outs):
+            np.testing.assert_array_equal(o.cpu().numpy(), plain.realize_sample(sd).cpu().numpy())
+        if flags & cmb3d.CMB3D_FLAG_STAGE_TIMING:
+            _, counts = cmb3d.cmb3d_stage_times(piped.handle)
+            assert list(counts) == [len(seeds)] * 4 + [0]
+        _, _, nbytes_piped = cmb3d.cmb3d_plan_info(piped.handle)
+        _, _, nbytes_plain = cmb3d.cmb3d_plan_info(plain.handle)
+        assert nbytes_piped - nbytes_plain == 4 * N ** 3 + 4 * N      # the second box
+
+
+def test_interleaved_field_spectrum_and_host_output():
+    N, L = 256, 2.2
+    kn, pk = smooth_pk(N, L)
+    kn2, pk2 = smooth_pk(N, L, amp=3e-3)
+    pix = cap_pixels(128, 0.25)
+    with cmb3d.Plan(N, L, 1.0, pix, 3, cmb3d.CMB3D_FLAG_PIPELINE) as piped, \
+            cmb3d.Plan(N, L, 1.0, pix, 3) as plain:
+        piped.set_pk(kn, pk)
+        plain.set_pk(kn, pk)
+        a0 = piped.realize_sample(1)
+        f = piped.realize_field(2)                           # whole field on the caller's stream
+        a1 = piped.realize_sample(3)
+        a2 = piped.realize_sample(4)
+        np.testing.assert_array_equal(a0.cpu().numpy(), plain.realize_sample(1).cpu().numpy())
+        np.testing.assert_array_equal(f.cpu().numpy(), plain.realize_field(2).cpu().numpy())
+        np.testing.assert_array_equal(a1.cpu().numpy(), plain.realize_sample(3).cpu().numpy())
+        np.testing.assert_array_equal(a2.cpu().numpy(), plain.realize_sample(4).cpu().numpy())
+        piped.realize_sample(5)                              # still in flight when the spectrum changes
+        piped.set_pk(kn2, pk2)
+        plain.set_pk(kn2, pk2)
+        b = piped.realize_sample(6)
+        np.testing.assert_array_equal(b.cpu().numpy(), plain.realize_sample(6).cpu().numpy())
+        host = np.empty(len(pix), np.float32)
+        for sd in (7, 8, 9):
+            cmb3d.cmb3d_realize_sample_to_host(piped.handle, sd, host)
+            np.testing.assert_array_equal(host, plain.realize_sample(sd).cpu().numpy())
+
+
+def test_autotune_on_first_pipelined_call():
+    N, L = 256, 2.2
+    kn, pk = smooth_pk(N, L)
+    pix = cap_pixels(128, 0.3)
+    with cmb3d.Plan(N, L, 1.0, pix, 3, cmb3d.CMB3D_FLAG_PIPELINE | cmb3d.CMB3D_FLAG_AUTOTUNE) as piped, \
+            cmb3d.Plan(N, L, 1.0, pix, 3) as plain:
+        piped.set_pk(kn, pk)
+        plain.set_pk(kn, pk)
+        outs = [piped.realize_sample(sd) for sd in (11, 12, 13)]
+        sched = cmb3d.cmb3d_plan_schedule(piped.handle)
+        sep = (sched[0], sched[1] if sched[1] >= 0 else 0, sched[2] if sched[2] >= 0 else 0, -1)
+        cmb3d.cmb3d_plan_set_schedule(plain.handle, sep)     # maps use the separate pruned passes
+        for sd, o in zip((11, 12, 13), outs):
+            np.testing.assert_array_equal(o.cpu().numpy(), plain.realize_sample(sd).cpu().numpy())
+
+
+def test_batch_of_pipelined_plans():
+    N, L = 256, 2.2
+    kn, pk = smooth_pk(N, L)
+    pixs = [cap_pixels(128, f) for f in (0.1, 0.3, 0.2)]
+    plans = [cmb3d.Plan(N, L, 1.0, p, 1, cmb3d.CMB3D_FLAG_PIPELINE) for p in pixs]
+    refs = [cmb3d.Plan(N, L, 1.0, p, 1) for p in pixs]
+    try:
+        for p in plans + refs:
+            p.set_pk(kn, pk)
+        first = plans[0].realize_sample(40)                  # pipelined work in flight
+        outs = [torch.empty(len(p), dtype=torch.float32, device="cuda") for p in pixs]
+        cmb3d.cmb3d_realize_sample_batch([p.handle for p in plans], [41, 42, 43], outs)
+        after = plans[0].realize_sample(44)
+        np.testing.assert_array_equal(first.cpu().numpy(), refs[0].realize_sample(40).cpu().numpy())
+        for sd, o, r in zip((41, 42, 43), outs, refs):
+            ref = r.realize_sample(sd).cpu().numpy().astype(np.float64)
+            assert np.max(np.abs(o.cpu().numpy() - ref)) <= 1e-6 * np.sqrt(np.mean(ref ** 2))
+        np.testing.assert_array_equal(after.cpu().numpy(), refs[0].realize_sample(44).cpu().numpy())
+    finally:
+        for p in plans + refs:
+            p.close()
