@@ -1,8 +1,10 @@
 """Build the cmb3d shared library (libcmb3d.so) in-tree for sm_103a.
 
 CUDA sources are compiled by nvcc with `-gencode arch=compute_103a,code=sm_103a`
-and host C++ by g++ with `-ffp-contract=off` (the FP64 pixel mapping must not
-be contracted into fused multiply-adds), in parallel, then linked by nvcc with
+and `-fmad=false` (no implicit multiply-add contraction: the kernels spell out
+their FMAs, so every kernel that inlines the same device code rounds it the
+same way), and host C++ by g++ with `-ffp-contract=off` (the FP64 pixel
+mapping must not be contracted either), in parallel, then linked by nvcc with
 the static CUDA runtime.  No cmake; a plain rebuild takes well under a minute.
 """
 from __future__ import annotations
@@ -71,7 +73,7 @@ def build(force: bool = False, ptxas_verbose: bool = False) -> str:
         obj = os.path.join(BUILD, f + ".o")
         objs.append(obj)
         if force or _stale(obj, src):
-            cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+            cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-fmad=false", "-std=c++17", "-Xcompiler", "-fPIC",
                    "-I", INCLUDE, "-I", CSRC, "-c", src, "-o", obj]
             if ptxas_verbose:
                 cmd += ["-Xptxas", "-v"]

@@ -21,6 +21,7 @@ namespace cmb3d {
 namespace {
 // keyp != NULL: the Philox key is read from device memory (graph replays
 // with new seeds); otherwise `key` is used.
+// One tile (m_x' tile blockIdx.x, row m_y = blockIdx.y) per block.
 template <int N, int R, int T>
 __global__ void __launch_bounds__(T*(N / R)) k_draw_zfft(float2* __restrict__ buf, const float* __restrict__ amp,
                                                          const float2* __restrict__ tw, uint2 key,

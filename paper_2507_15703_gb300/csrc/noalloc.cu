@@ -82,9 +82,9 @@ struct W<3> {
   static constexpr int K = 4, OFF = -1;
   static __device__ __forceinline__ void run(float t, float* w) {
     const float t2 = t * t;
-    w[0] = 0.5f * ((2.0f - t) * t - 1.0f) * t;
-    w[1] = 0.5f * ((3.0f * t - 5.0f) * t2 + 2.0f);
-    w[2] = 0.5f * (((4.0f - 3.0f * t) * t) + 1.0f) * t;
+    w[0] = 0.5f * fmaf(2.0f - t, t, -1.0f) * t;
+    w[1] = 0.5f * fmaf(fmaf(3.0f, t, -5.0f), t2, 2.0f);
+    w[2] = 0.5f * fmaf(fmaf(-3.0f, t, 4.0f), t, 1.0f) * t;
     w[3] = 0.5f * (t - 1.0f) * t2;
   }
 };

@@ -1,10 +1,10 @@
 """The batched form: many boxes with their own pixel sets in one persistent
 launch replayed from a CUDA graph.
 
-Each map of a batch must equal the map the single-plan entry point makes with
-the same kernel shapes (to 1e-6 of rms: the same arithmetic, compiled into a
-different kernel, may contract into fused multiply-adds differently), and
-match the FP64 oracle; a batch
+Each map of a batch must equal, bit for bit, the map the single-plan entry
+point makes with the same kernel shapes (the same device code, compiled
+without implicit contraction, rounds identically in every kernel), and match
+the FP64 oracle; a batch
 replays with new seeds; an injected withheld producer makes the bounded waits
 give up with CMB3D_ETIMEOUT while the context stays usable.
 """
@@ -30,7 +30,11 @@ def _gpu():
     cmb3d.load()
 
 
-def close(a, b, tol=1e-6):
+def close(a, b, tol=0.0):
+    """Bit for bit (tol = 0), or max |a - b| <= tol * rms(b) across kernel shapes."""
+    if tol == 0.0:
+        np.testing.assert_array_equal(np.asarray(a), np.asarray(b))
+        return
     a = np.asarray(a, np.float64)
     b = np.asarray(b, np.float64)
     assert np.max(np.abs(a - b)) <= tol * np.sqrt(np.mean(b ** 2))
@@ -105,7 +109,7 @@ def test_batch_autotune_and_variants_agree():
     ref = [o.cpu().numpy() for o in outs]
     cmb3d.cmb3d_realize_sample_batch([p.handle for p in plans], [5, 6, 7], outs)
     for o, r in zip(outs, ref):
-        close(o.cpu().numpy(), r)
+        close(o.cpu().numpy(), r, 1e-6)        # the tuned plan may pick other radices
     tuned.close()
     for p in plans:
         p.close()

@@ -112,8 +112,7 @@ def test_batch_of_pipelined_plans():
         after = plans[0].realize_sample(44)
         np.testing.assert_array_equal(first.cpu().numpy(), refs[0].realize_sample(40).cpu().numpy())
         for sd, o, r in zip((41, 42, 43), outs, refs):
-            ref = r.realize_sample(sd).cpu().numpy().astype(np.float64)
-            assert np.max(np.abs(o.cpu().numpy() - ref)) <= 1e-6 * np.sqrt(np.mean(ref ** 2))
+            np.testing.assert_array_equal(o.cpu().numpy(), r.realize_sample(sd).cpu().numpy())
         np.testing.assert_array_equal(after.cpu().numpy(), refs[0].realize_sample(44).cpu().numpy())
     finally:
         for p in plans + refs:
