@@ -234,7 +234,7 @@ def run_cuda(args, rank, world, local):
     setup_s = time.time() - t0
     stream = torch.cuda.current_stream(dev)
     out = torch.empty(npix, dtype=torch.float32, device=dev)
-    seed0 = 1000003 * rank
+    seed0 = rank_seed_base(rank)
 
     dist = init_dist(world, dev)
 
@@ -316,7 +316,7 @@ def run_cuda(args, rank, world, local):
         return
 
     maps = world * args.steps
-    value = maps / (t_max / 1e3)
+    value = job_throughput(world, args.steps, t_max)
     ab = algorithmic_bytes(w.N, npix, n_planes, n_rows)
     names = cmb3d.STAGE_NAMES
     kernels = {}
@@ -440,7 +440,7 @@ def run_cuda_batch(args, rank, world, local, w):
     outs = [torch.empty(n, dtype=torch.float32, device=dev) for n in npix]
     stream = torch.cuda.current_stream(dev)
     dist = init_dist(world, dev)
-    base = 1000003 * rank
+    base = rank_seed_base(rank)
 
     def step(i):
         cmb3d.cmb3d_realize_sample_batch(handles, [base + i * w.batch + b for b in range(w.batch)], outs, stream)
@@ -502,7 +502,7 @@ def run_cuda_batch(args, rank, world, local, w):
         finish_dist(dist)
         return
     maps = world * args.steps * w.batch
-    value = maps / (t_max / 1e3)
+    value = job_throughput(world, args.steps * w.batch, t_max)
     batch_bytes = 24 * sum(npix)
     for zp, rw in extents:
         ab = algorithmic_bytes(w.N, 0, zp, rw)
@@ -525,10 +525,15 @@ def run_cuda_batch(args, rank, world, local, w):
 
 
 def init_dist(world, dev):
+    """Process group of the replicas (RANK / WORLD_SIZE / MASTER_* from the
+    environment): NCCL on the GPUs, gloo when dev is None (host-side tests)."""
     if world <= 1:
         return None
     import torch.distributed as dist
-    dist.init_process_group("nccl", device_id=dev)
+    if dev is None:
+        dist.init_process_group("gloo")
+    else:
+        dist.init_process_group("nccl", device_id=dev)
     return dist
 
 
@@ -538,12 +543,27 @@ def finish_dist(dist):
 
 
 def max_over_ranks(dist, v, dev):
+    """The largest of every rank's v (the job's time is its slowest rank)."""
     if dist is None:
         return v
     import torch
-    t = torch.tensor([v], device=dev, dtype=torch.float64)
+    t = torch.tensor([v], device=dev if dev is not None else "cpu", dtype=torch.float64)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+SEED_STRIDE = 1000003
+
+
+def rank_seed_base(rank: int) -> int:
+    """First seed of a replica: ranks draw disjoint seed ranges as long as a
+    run uses fewer than SEED_STRIDE seeds per rank."""
+    return SEED_STRIDE * rank
+
+
+def job_throughput(world: int, units_per_rank: int, t_max_ms: float) -> float:
+    """Whole-job units per second: all ranks' units over the slowest rank's time."""
+    return world * units_per_rank / (t_max_ms / 1e3)
 
 
 def kernel_entry(n, total_ms, all_ms, alg_bytes):
