@@ -66,7 +66,7 @@ def gamma_matrix(col: np.ndarray, h: int) -> np.ndarray:
     """R3: the h x h Toeplitz covariance from the P_box column (length M)."""
     xi = np.fft.ifft(col, norm="forward").real        # sum_mz col[mz] e^{+2 pi i mz d / M}
     d = np.abs(np.arange(h)[:, None] - np.arange(h)[None, :])
-    return xi[d]
+    return xi[d % col.size]                           # xi is periodic in d with the z-period M
 
 
 def sqrt_psd(g: np.ndarray) -> np.ndarray:
