@@ -131,6 +131,56 @@ int cmb3d_plan(cmb3d_plan_t* out, int N, double L, double r,
                const double* pix_xyz, int64_t npix, int interp, uint32_t flags);
 
 /*
+ * Create a plan for the 2-D Fourier method (paper Sec. II.D.2): the box is
+ * simulated in Fourier space along x and y and in real space along z, on the
+ * h layers that hold the cap only.  For each (m_x, m_y) the h values are
+ * correlated Gaussians, S c with S the symmetric square root of the h x h
+ * covariance Gamma_ij = xi(|i - j| dp) along z (xi: the transform of the box
+ * spectrum along m_z over the z-period M dp) and c complex normals; a 2-D
+ * inverse FFT per layer gives the real layers, which are sampled at the
+ * pixels as in the 3-D method.  The cap is not required to fit in a cube:
+ * x and y are periodic with side L, z is not.
+ *
+ *   N        points along x and y; a power of two with 16 <= N <= 2048.
+ *   M        z-period in grid steps (the never-built N x N x M box of
+ *            Sec. II.C), 1 <= M <= 65536.
+ *   h        simulated layers, 1 <= h <= 32 and h <= N (else
+ *            CMB3D_EUNSUPPORTED); layer j sits at z = z0 + j L/N.
+ *   L, r     side of the box in x and y, sphere radius; finite and > 0.
+ *   z0       height of layer 0, finite.
+ *   pix_xyz, npix, interp as for cmb3d_plan.  A pixel maps to
+ *            u = ((r n_x + L/2), (r n_y + L/2), (r n_z - z0)) / (L/N) in IEEE
+ *            double with no fused multiply-add; its interpolation stencil
+ *            must lie inside the h layers (layers floor(u_z) - 1 .. + 2 for
+ *            tricubic, floor(u_z) .. + 1 for trilinear), else CMB3D_EINVAL.
+ *   flags    CMB3D_FLAG_NO_SORT, ALLOW_WRAP (accepted; x and y always wrap),
+ *            STAGE_TIMING, AUTOTUNE (y and x shapes), NO_PRUNE, PIPELINE;
+ *            FUSED_YX and FP16_GEMM give CMB3D_EUNSUPPORTED.
+ * The plan is used with the same calls as a 3-D plan: cmb3d_set_spectrum,
+ * cmb3d_realize_sample(_to_host), cmb3d_realize_field (h x N x N floats),
+ * cmb3d_draw_spectrum (the hybrid layers T^[z][m_y][m_x'], h x N x N/2
+ * float2, m_x' = 0 packing T^(0, .) + i T^(N/2, .)), cmb3d_stage_times (the
+ * draw of the correlated layers is reported as stage 0).  Batches of 2-D
+ * plans run map by map.
+ */
+int cmb3d_plan_2d(cmb3d_plan_t* out, int N, int M, int h, double L, double r, double z0,
+                  const double* pix_xyz, int64_t npix, int interp, uint32_t flags);
+
+/*
+ * The per-(m_x, m_y) factors of the 2-D method (host only): for every
+ * q = m_x^2 + m_y^2 in [0, 2 (N/2)^2] reached by m_x in [0, N/2], m_y signed
+ * in (-N/2, N/2], out[(q h + z) h + i] = S[z][i], the symmetric square root
+ * (eigendecomposition, cyclic Jacobi in FP64, negative eigenvalues set to 0)
+ * of Gamma_ij = sum_{m_z < M} P_box(m) cos(2 pi m_z (i - j) / M) with
+ * P_box(m) = P_inf(|k|) (2 pi / dp)^3 / (M N^2), dp = L / N,
+ * k = (2 pi m_x/(N dp), 2 pi m_y/(N dp), 2 pi m_z/(M dp)) (paper Eq. 2.11 for
+ * an N x N x M box) and P_box(0) = 0; unreached q are zero.  P_inf is linear
+ * in k between the n nodes (k, pk) as in cmb3d_set_spectrum.  out: host,
+ * (2 (N/2)^2 + 1) h^2 floats.
+ */
+int cmb3d_gamma_sqrt_table(int N, int M, int h, double L, const double* k, const double* pk, int n, float* out);
+
+/*
  * Set the box spectrum (paper Sec. II.A-C).
  *
  *   kind = CMB3D_SPEC_PK: x[0..n) are strictly increasing k >= 0 and y[0..n)

@@ -58,6 +58,9 @@ _dp = C.POINTER(C.c_double)
 # name -> (restype, argtypes); the full exported surface of include/cmb3d.h
 PROTOTYPES = {
     "cmb3d_plan": (_i32, [C.POINTER(_vp), _i32, C.c_double, C.c_double, _dp, _i64, _i32, _u32]),
+    "cmb3d_plan_2d": (_i32, [C.POINTER(_vp), _i32, _i32, _i32, C.c_double, C.c_double, C.c_double, _dp, _i64,
+                             _i32, _u32]),
+    "cmb3d_gamma_sqrt_table": (_i32, [_i32, _i32, _i32, C.c_double, _dp, _dp, _i32, C.POINTER(C.c_float)]),
     "cmb3d_set_spectrum": (_i32, [_vp, _i32, _dp, _dp, _i32, _i32, _dp]),
     "cmb3d_fit_pk": (_i32, [_dp, _dp, _i32, _i32, C.c_double, C.c_double, _i32, _dp, _dp, _dp]),
     "cmb3d_get_pk": (_i32, [_vp, _dp, _dp, _i32]),
@@ -166,6 +169,28 @@ def cmb3d_plan(N: int, L: float, r: float, pix_xyz, interp: int = CMB3D_TRILINEA
     _check(lib.cmb3d_plan(C.byref(h), int(N), float(L), float(r), ptr, pix.shape[0], int(interp), int(flags)),
            "cmb3d_plan")
     return h.value
+
+
+def cmb3d_plan_2d(N: int, M: int, h: int, L: float, r: float, z0: float, pix_xyz, interp: int = CMB3D_TRILINEAR,
+                  flags: int = CMB3D_FLAG_NONE) -> int:
+    lib = load()
+    pix = _f64(pix_xyz).reshape(-1, 3)
+    hd = _vp()
+    ptr = pix.ctypes.data_as(_dp) if pix.size else None
+    _check(lib.cmb3d_plan_2d(C.byref(hd), int(N), int(M), int(h), float(L), float(r), float(z0), ptr, pix.shape[0],
+                             int(interp), int(flags)), "cmb3d_plan_2d")
+    return hd.value
+
+
+def cmb3d_gamma_sqrt_table(N: int, M: int, h: int, L: float, k, pk) -> np.ndarray:
+    """float32 [(2 (N/2)^2 + 1), h, h]: the 2-D method's per-q square roots."""
+    lib = load()
+    ka, pa = _f64(k), _f64(pk)
+    out = np.zeros((2 * (N // 2) ** 2 + 1, h, h), dtype=np.float32)
+    _check(lib.cmb3d_gamma_sqrt_table(int(N), int(M), int(h), float(L), ka.ctypes.data_as(_dp),
+                                      pa.ctypes.data_as(_dp), ka.size, out.ctypes.data_as(C.POINTER(C.c_float))),
+           "cmb3d_gamma_sqrt_table")
+    return out
 
 
 def cmb3d_set_spectrum(plan: int, kind: int, x, y, nkbins: int = 256) -> float:
@@ -453,3 +478,28 @@ class Plan:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Plan2D(Plan):
+    """Plan of the 2-D Fourier method (h layers of N x N, z-period M, layer 0
+    at z0); the same calls as Plan, with the field and hybrid spectrum shaped
+    by the layers."""
+
+    def __init__(self, N, M, h, L, r, z0, pix_xyz, interp=CMB3D_TRILINEAR, flags=CMB3D_FLAG_NONE):
+        self.handle = cmb3d_plan_2d(N, M, h, L, r, z0, pix_xyz, interp, flags)
+        self.N, self.M, self.h = int(N), int(M), int(h)
+        self.npix = int(np.asarray(pix_xyz).reshape(-1, 3).shape[0])
+
+    def realize_field(self, seed, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty((self.h, self.N, self.N), dtype=torch.float32, device="cuda")
+        cmb3d_realize_field(self.handle, seed, out, stream)
+        return out
+
+    def draw_spectrum(self, seed, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty((self.h, self.N, self.N // 2, 2), dtype=torch.float32, device="cuda")
+        cmb3d_draw_spectrum(self.handle, seed, out, stream)
+        return out

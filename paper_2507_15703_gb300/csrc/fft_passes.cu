@@ -278,14 +278,13 @@ cudaError_t run_xc2r(float2* buf, const float2* tw, cudaStream_t s, const int32_
   constexpr int N2 = N / 2, NB = N2 / R;
   constexpr int ROWS0 = THREADS / NB > 0 ? THREADS / NB : 1;
   constexpr int ROWS = ROWS0 < N * N ? ROWS0 : N * N;
-  static_assert(N < 128 || kRowListPad % ROWS == 0, "row lists are padded to whole blocks of every row variant");
+  static_assert(N < 128 || kRowListPad % ROWS == 0, "pruned row lists are padded to whole blocks of every shape");
   constexpr int P = N2 + (N2 >> 4);
   const size_t smem = sizeof(float2) * P * ROWS;
   auto kern = k_xc2r<N, R, ROWS>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
-  if (rows && N < 128) return cudaErrorNotSupported;
-  if (rows && (nrows <= 0 || nrows % kRowListPad != 0)) return nrows == 0 ? cudaSuccess : cudaErrorInvalidValue;
+  if (rows && (nrows <= 0 || nrows % ROWS != 0)) return nrows == 0 ? cudaSuccess : cudaErrorInvalidValue;
   const int64_t nb = rows ? nrows / ROWS : static_cast<int64_t>(N) * N / ROWS;
   kern<<<dim3(static_cast<unsigned>(nb)), ROWS * NB, smem, s>>>(buf, tw, rows);
   return cudaGetLastError();

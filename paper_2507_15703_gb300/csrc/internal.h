@@ -22,6 +22,10 @@ int num_fused_variants(int N);
 cudaError_t launch_draw_zfft(int N, int v, float2* buf, const float* amp, const float2* tw,
                              uint64_t seed, cudaStream_t s, const uint2* key_dev = nullptr);
 
+// 2-D Fourier method: the hybrid layers [z][m_y][m_x'] (h <= 32 layers) from
+// the per-q table of z-covariance square roots (h x h floats per q).
+cudaError_t launch_draw2d(int N, int h, float2* buf, const float* tab, uint64_t seed, cudaStream_t s);
+
 // Diagnostic: the drawn packed half spectrum [m_z][m_y][m_x'], untransformed.
 cudaError_t launch_draw_only(int N, float2* buf, const float* amp, uint64_t seed, cudaStream_t s);
 
@@ -45,9 +49,11 @@ bool yfft_gemm_supported(int N);
 cudaError_t launch_yfft_gemm(int N, float2* buf, const float2* tw, unsigned* err, cudaStream_t s);
 
 // Complex-to-real inverse FFT of every (z, y) row along x, in place.
-// With `rows` (N >= 128; row indices z N + y, nrows a multiple of kRowListPad)
+// With `rows` (row indices z N + y, nrows a multiple of the shape's rows per
+// block: kRowListPad covers every shape for N >= 128, kRowListPadAny every N)
 // only the listed rows are transformed; padding entries must name a scratch row.
 constexpr int kRowListPad = 64;
+constexpr int kRowListPadAny = 256;
 cudaError_t launch_xc2r(int N, int v, float2* buf, const float2* tw, cudaStream_t s, const int32_t* rows = nullptr,
                         int64_t nrows = 0);
 

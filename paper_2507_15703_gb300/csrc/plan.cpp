@@ -10,6 +10,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <thread>
 #include <utility>
 #include <vector>
 
@@ -131,6 +132,18 @@ struct cmb3d_plan_s {
   cudaStream_t dstream = nullptr, pstream = nullptr;
   cudaEvent_t ev_drawn[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr}, ev_call = nullptr;
   int next_box = 0;
+  // The 2-D Fourier method (method 2; 3 = the 3-D method): h layers of N x N,
+  // z-period M, layer 0 at z0; the per-q square roots of the z-covariance
+  // (sqt) replace the amplitude table, and the passes run on plane and row
+  // lists that cover the layers (d_planes_all, d_rows_all) or, for sky maps,
+  // the pruned lists.
+  int method = 3;
+  int M = 0, h = 0;
+  double z0 = 0.0;
+  float* sqt = nullptr;
+  int32_t* d_planes_all = nullptr;
+  int32_t* d_rows_all = nullptr;
+  int64_t nrows_all_pad = 0;
 };
 
 namespace {
@@ -182,6 +195,9 @@ void free_plan(cmb3d_plan_s* p) {
   cudaFree(p->d_planes);
   cudaFree(p->d_rows);
   cudaFree(p->d_rowmask);
+  cudaFree(p->sqt);
+  cudaFree(p->d_planes_all);
+  cudaFree(p->d_rows_all);
   for (auto& r : p->recs) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -296,6 +312,28 @@ float time_launches(cudaStream_t s, F f, bool* ok) {
 
 int autotune(cmb3d_plan_s* p, cudaStream_t s) {
   const int N = p->N;
+  if (p->method == 2) {                               // y and x shapes on the layer lists
+    Schedule best;
+    bool ok = true;
+    float ty = 1e30f, tx = 1e30f;
+    for (int v = 0; v < cmb3d::num_col_variants(N); ++v) {
+      const float t = time_launches(s, [&] {
+        return cmb3d::launch_yfft(N, v, p->buf, p->tw, s, p->d_planes_all, p->h, nullptr);
+      }, &ok);
+      if (!ok) return fail_cuda(cudaErrorLaunchFailure, "autotune yfft");
+      if (t < ty) ty = t, best.y = v;
+    }
+    for (int v = 0; v < cmb3d::num_row_variants(N); ++v) {
+      const float t = time_launches(s, [&] {
+        return cmb3d::launch_xc2r(N, v, p->buf, p->tw, s, p->d_rows_all, p->nrows_all_pad);
+      }, &ok);
+      if (!ok) return fail_cuda(cudaErrorLaunchFailure, "autotune xc2r");
+      if (t < tx) tx = t, best.x = v;
+    }
+    p->sched = best;
+    p->tuned = true;
+    return CMB3D_OK;                                  // not cached: the layer count is per plan
+  }
   const int restrict_bits = p->flags & (CMB3D_FLAG_THREE_PASS | CMB3D_FLAG_FUSED_YX);
   const std::pair<int, int> key(p->device, N * 16 + restrict_bits);
   {
@@ -351,8 +389,10 @@ int ensure_tuned(cmb3d_plan_s* p, cudaStream_t s) {
 // Draw fused with the z pass into `box`.
 int run_draw(cmb3d_plan_s* p, uint64_t seed, cudaStream_t s, float2* box) {
   const Schedule& sc = p->sched;
-  cudaError_t e = timed(p, CMB3D_STAGE_DRAW_ZFFT, s,
-                        [&] { return cmb3d::launch_draw_zfft(p->N, sc.draw, box, p->amp, p->tw, seed, s); });
+  cudaError_t e = timed(p, CMB3D_STAGE_DRAW_ZFFT, s, [&] {
+    if (p->method == 2) return cmb3d::launch_draw2d(p->N, p->h, box, p->sqt, seed, s);
+    return cmb3d::launch_draw_zfft(p->N, sc.draw, box, p->amp, p->tw, seed, s);
+  });
   if (e != cudaSuccess) return fail_cuda(e, "draw_zfft launch");
   return CMB3D_OK;
 }
@@ -364,6 +404,21 @@ int run_draw(cmb3d_plan_s* p, uint64_t seed, cudaStream_t s, float2* box) {
 int run_passes(cmb3d_plan_s* p, cudaStream_t s, bool prune, float2* box) {
   const Schedule& sc = p->sched;
   cudaError_t e;
+  if (p->method == 2) {                               // the h layers: y and x passes on lists
+    const bool pr = prune && p->prune;
+    const int yv = sc.y >= 0 ? sc.y : 0, xv = sc.x >= 0 ? sc.x : 0;
+    e = timed(p, CMB3D_STAGE_YFFT, s, [&] {
+      return cmb3d::launch_yfft(p->N, yv, box, p->tw, s, pr ? p->d_planes : p->d_planes_all,
+                                static_cast<int>(pr ? p->nplanes : p->h), pr ? p->d_rowmask : nullptr);
+    });
+    if (e != cudaSuccess) return fail_cuda(e, "yfft launch");
+    e = timed(p, CMB3D_STAGE_XC2R, s, [&] {
+      return cmb3d::launch_xc2r(p->N, xv, box, p->tw, s, pr ? p->d_rows : p->d_rows_all,
+                                pr ? p->nrows_pad : p->nrows_all_pad);
+    });
+    if (e != cudaSuccess) return fail_cuda(e, "xc2r launch");
+    return CMB3D_OK;
+  }
   if (prune && p->prune) {
     const int yv = sc.y >= 0 ? sc.y : 0, xv = sc.x >= 0 ? sc.x : 0;
     e = timed(p, CMB3D_STAGE_YFFT, s, [&] {
@@ -462,13 +517,24 @@ const char* cmb3d_strerror(int status) {
 
 const char* cmb3d_error_detail(void) { return g_detail.c_str(); }
 
-int cmb3d_plan(cmb3d_plan_t* out, int N, double L, double r, const double* pix_xyz, int64_t npix, int interp,
-               uint32_t flags) {
+// Plan of the 3-D method (method 3) or of the 2-D Fourier method (method 2,
+// with M, h, z0); the two share the pixel table, pruning and the passes.
+static int create_plan(cmb3d_plan_t* out, int method, int N, int M, int h, double L, double r, double z0,
+                       const double* pix_xyz, int64_t npix, int interp, uint32_t flags) {
   if (!out) return fail(CMB3D_EINVAL, "out is NULL");
   *out = nullptr;
-  if (!is_pow2(N) || N < 8 || N > 2048) return fail(CMB3D_EUNSUPPORTED, "N must be a power of two in [8, 2048]");
+  if (method == 2) {
+    if (!is_pow2(N) || N < 16 || N > 2048) return fail(CMB3D_EUNSUPPORTED, "N must be a power of two in [16, 2048]");
+    if (h < 1 || h > 32 || h > N) return fail(CMB3D_EUNSUPPORTED, "h must satisfy 1 <= h <= 32 and h <= N");
+    if (M < 1 || M > 65536) return fail(CMB3D_EINVAL, "M must be in [1, 65536]");
+    if (!std::isfinite(z0)) return fail(CMB3D_EINVAL, "z0 must be finite");
+    if (flags & (CMB3D_FLAG_FUSED_YX | CMB3D_FLAG_FP16_GEMM))
+      return fail(CMB3D_EUNSUPPORTED, "the 2-D method runs the separate FP32 y and x passes");
+  } else if (!is_pow2(N) || N < 8 || N > 2048) {
+    return fail(CMB3D_EUNSUPPORTED, "N must be a power of two in [8, 2048]");
+  }
   if (!(std::isfinite(L) && L > 0) || !(std::isfinite(r) && r > 0)) return fail(CMB3D_EINVAL, "L and r must be finite and > 0");
-  if (!(L > 2.0 * r) && !(flags & CMB3D_FLAG_ALLOW_WRAP))
+  if (method == 3 && !(L > 2.0 * r) && !(flags & CMB3D_FLAG_ALLOW_WRAP))
     return fail(CMB3D_EINVAL, "L must exceed 2r (set CMB3D_FLAG_ALLOW_WRAP to allow wrapping)");
   if (npix < 0 || npix >= (int64_t(1) << 31)) return fail(CMB3D_EINVAL, "npix out of range");
   if (npix > 0 && !pix_xyz) return fail(CMB3D_EINVAL, "pix_xyz is NULL");
@@ -492,6 +558,11 @@ int cmb3d_plan(cmb3d_plan_t* out, int N, double L, double r, const double* pix_x
   p->interp = interp;
   p->flags = flags;
   p->npix = npix;
+  p->method = method;
+  p->M = M;
+  p->h = h;
+  p->z0 = z0;
+  const int nz = method == 2 ? h : N;                 // z-planes of the box buffer
   if ((flags & CMB3D_FLAG_FUSED_YX) && cmb3d::num_fused_variants(N) > 0) p->sched.fused = 0;
   if (flags & CMB3D_FLAG_FP16_GEMM) {
     if (gemm_y_variant(N) < 0) {
@@ -510,7 +581,8 @@ int cmb3d_plan(cmb3d_plan_t* out, int N, double L, double r, const double* pix_x
   std::vector<float4> tab;
   std::vector<int32_t> perm;
   std::vector<uint32_t> rowmask;
-  std::vector<int32_t> planes, rows;
+  std::vector<int32_t> planes, rows, planes_all, rows_all;
+  bool outside = false;                               // 2-D: a stencil leaves the layers
   try {
     tab.resize(static_cast<size_t>(npix));
     std::vector<std::pair<uint64_t, int32_t>> order;
@@ -523,11 +595,21 @@ int cmb3d_plan(cmb3d_plan_t* out, int N, double L, double r, const double* pix_x
       uint32_t b[3];
       float t[3];
       for (int a = 0; a < 3; ++a) {
-        const double u = (r * pix_xyz[3 * i + a] + half_l) / dp;
+        const double u = (r * pix_xyz[3 * i + a] + (method == 2 && a == 2 ? -z0 : half_l)) / dp;
         const double fl = std::floor(u);
         const double frac = u - fl;
-        int64_t bi = static_cast<int64_t>(fl) % N;
-        if (bi < 0) bi += N;
+        int64_t bi;
+        if (method == 2 && a == 2) {                  // layers: no wrap, whole stencil inside
+          bi = fl >= -2.0 && fl <= 2048.0 ? static_cast<int64_t>(fl) : -8;
+          const int64_t lo = interp == CMB3D_TRICUBIC ? bi - 1 : bi, hi = interp == CMB3D_TRICUBIC ? bi + 2 : bi + 1;
+          if (lo < 0 || hi > h - 1) {
+            outside = true;
+            bi = 0;
+          }
+        } else {
+          bi = static_cast<int64_t>(fl) % N;
+          if (bi < 0) bi += N;
+        }
         b[a] = static_cast<uint32_t>(bi);
         t[a] = static_cast<float>(frac);
       }
@@ -591,17 +673,26 @@ int cmb3d_plan(cmb3d_plan_t* out, int N, double L, double r, const double* pix_x
         }
         if (any) planes.push_back(z);
       }
-      if (static_cast<int64_t>(rows.size()) == static_cast<int64_t>(N) * N) {   // nothing to prune
+      if (static_cast<int64_t>(rows.size()) == static_cast<int64_t>(nz) * N) {   // nothing to prune
         rows.clear();
         planes.clear();
         rowmask.clear();
       } else {
-        while (rows.size() % cmb3d::kRowListPad) rows.push_back(N * N);   // scratch row past the box
+        while (rows.size() % cmb3d::kRowListPad) rows.push_back(nz * N);   // scratch row past the box
       }
+    }
+    if (method == 2) {                                // every layer and row, for whole layers
+      for (int z = 0; z < h; ++z) planes_all.push_back(z);
+      for (int rr = 0; rr < h * N; ++rr) rows_all.push_back(rr);
+      while (rows_all.size() % cmb3d::kRowListPadAny) rows_all.push_back(h * N);
     }
   } catch (const std::bad_alloc&) {
     delete p;
     return fail(CMB3D_ENOMEM, "host allocation of the pixel table");
+  }
+  if (outside) {
+    delete p;
+    return fail(CMB3D_EINVAL, "a pixel's interpolation stencil leaves the h simulated layers");
   }
 
   // ---- twiddles exp(+2 pi i m / N), FP64 rounded once to FP32 -------------
@@ -611,11 +702,13 @@ int cmb3d_plan(cmb3d_plan_t* out, int N, double L, double r, const double* pix_x
     tw[static_cast<size_t>(m)] = make_float2(static_cast<float>(std::cos(ang)), static_cast<float>(std::sin(ang)));
   }
 
-  const size_t nbuf = static_cast<size_t>(N) * N * (N / 2) + (N / 2);   // + the scratch row
-  const size_t nq = 3 * static_cast<size_t>(N / 2) * (N / 2) + 1;
+  const size_t nbuf = static_cast<size_t>(nz) * N * (N / 2) + (N / 2);   // + the scratch row
+  const size_t nq = method == 2 ? 0 : 3 * static_cast<size_t>(N / 2) * (N / 2) + 1;
   int st;
   if ((st = dev_alloc(p, &p->buf, nbuf, "box")) != CMB3D_OK ||
       (st = dev_alloc(p, &p->amp, nq, "amplitude table")) != CMB3D_OK ||
+      (st = dev_alloc(p, &p->d_planes_all, planes_all.size(), "layer list")) != CMB3D_OK ||
+      (st = dev_alloc(p, &p->d_rows_all, rows_all.size(), "layer row list")) != CMB3D_OK ||
       (st = dev_alloc(p, &p->tw, static_cast<size_t>(N), "twiddles")) != CMB3D_OK ||
       (st = dev_alloc(p, &p->tab, static_cast<size_t>(npix), "pixel table")) != CMB3D_OK ||
       (st = dev_alloc(p, &p->outbuf, static_cast<size_t>(npix), "output staging")) != CMB3D_OK ||
@@ -633,6 +726,12 @@ int cmb3d_plan(cmb3d_plan_t* out, int N, double L, double r, const double* pix_x
     e = cudaMemcpy(p->tab, tab.data(), tab.size() * sizeof(float4), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && !perm.empty())
     e = cudaMemcpy(p->perm, perm.data(), perm.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !rows_all.empty()) {
+    e = cudaMemcpy(p->d_planes_all, planes_all.data(), planes_all.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(p->d_rows_all, rows_all.data(), rows_all.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    p->nrows_all_pad = static_cast<int64_t>(rows_all.size());
+  }
   if (e == cudaSuccess && !rows.empty()) {
     e = cudaMemcpy(p->d_rows, rows.data(), rows.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
@@ -643,7 +742,7 @@ int cmb3d_plan(cmb3d_plan_t* out, int N, double L, double r, const double* pix_x
     p->nplanes = static_cast<int64_t>(planes.size());
     p->nrows_pad = static_cast<int64_t>(rows.size());
     p->nrows = 0;
-    for (int32_t r : rows) p->nrows += r < N * N ? 1 : 0;
+    for (int32_t rr : rows) p->nrows += rr < nz * N ? 1 : 0;
   }
   if (e == cudaSuccess && (flags & CMB3D_FLAG_PIPELINE)) {
     if ((st = dev_alloc(p, &p->buf2, nbuf, "second box")) != CMB3D_OK) {
@@ -664,6 +763,16 @@ int cmb3d_plan(cmb3d_plan_t* out, int N, double L, double r, const double* pix_x
   }
   *out = p;
   return CMB3D_OK;
+}
+
+int cmb3d_plan(cmb3d_plan_t* out, int N, double L, double r, const double* pix_xyz, int64_t npix, int interp,
+               uint32_t flags) {
+  return create_plan(out, 3, N, 0, 0, L, r, 0.0, pix_xyz, npix, interp, flags);
+}
+
+int cmb3d_plan_2d(cmb3d_plan_t* out, int N, int M, int h, double L, double r, double z0, const double* pix_xyz,
+                  int64_t npix, int interp, uint32_t flags) {
+  return create_plan(out, 2, N, M, h, L, r, z0, pix_xyz, npix, interp, flags);
 }
 
 namespace {
@@ -721,6 +830,53 @@ int cmb3d_cl_matrix(const double* ell, int n, const double* knodes, int nk, doub
   return CMB3D_OK;
 }
 
+// The 2-D method's per-q square roots of the z-covariance (host FP64, then
+// FP32 on the device) from P_inf on the nodes (kn, pn).
+static int set_spectrum_2d(cmb3d_plan_s* p, std::vector<double>& kn, std::vector<double>& pn, double err,
+                           double* fit_err) {
+  const int N = p->N, h = p->h;
+  std::vector<float> table;
+  try {
+    const unsigned hc = std::thread::hardware_concurrency();
+    cmb3d::sqrt_gamma_table(N, p->M, h, p->L, kn, pn, static_cast<int>(std::max(1u, std::min(hc, 32u))), &table);
+  } catch (const std::bad_alloc&) {
+    return fail(CMB3D_ENOMEM, "host allocation of the z-covariance table");
+  }
+  DeviceGuard g(p->device);
+  cudaError_t e = drain_pipeline(p);                 // no draw of the plan still reads the table
+  if (e != cudaSuccess) return fail_cuda(e, "pipeline drain");
+  if (!p->sqt) {
+    int st = dev_alloc(p, &p->sqt, table.size(), "z-covariance table");
+    if (st != CMB3D_OK) return st;
+  }
+  e = cudaMemcpy(p->sqt, table.data(), table.size() * sizeof(float), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return fail_cuda(e, "z-covariance table upload");
+  p->knodes.swap(kn);
+  p->pnodes.swap(pn);
+  p->has_spec = true;
+  if (fit_err) *fit_err = err;
+  return CMB3D_OK;
+}
+
+int cmb3d_gamma_sqrt_table(int N, int M, int h, double L, const double* k, const double* pk, int n, float* out) {
+  if (!is_pow2(N) || N < 2 || N > 2048 || M < 1 || M > 65536 || h < 1 || h > 64)
+    return fail(CMB3D_EINVAL, "N (power of two), M or h out of range");
+  if (!(std::isfinite(L) && L > 0) || !k || !pk || n < 1 || !out) return fail(CMB3D_EINVAL, "bad arguments");
+  for (int i = 0; i < n; ++i)
+    if (!std::isfinite(k[i]) || !std::isfinite(pk[i]) || k[i] < 0 || pk[i] < 0 || (i > 0 && !(k[i] > k[i - 1])))
+      return fail(CMB3D_EINVAL, "k must increase; k and P(k) finite and >= 0");
+  try {
+    std::vector<float> table;
+    const unsigned hc = std::thread::hardware_concurrency();
+    cmb3d::sqrt_gamma_table(N, M, h, L, std::vector<double>(k, k + n), std::vector<double>(pk, pk + n),
+                            static_cast<int>(std::max(1u, std::min(hc, 32u))), &table);
+    std::copy(table.begin(), table.end(), out);
+  } catch (const std::bad_alloc&) {
+    return fail(CMB3D_ENOMEM, "host allocation of the z-covariance table");
+  }
+  return CMB3D_OK;
+}
+
 int cmb3d_set_spectrum(cmb3d_plan_t p, int kind, const double* x, const double* y, int n, int nkbins,
                        double* fit_err) {
   if (!p) return fail(CMB3D_EINVAL, "plan is NULL");
@@ -748,6 +904,7 @@ int cmb3d_set_spectrum(cmb3d_plan_t p, int kind, const double* x, const double* 
     return fail(CMB3D_EINVAL, "kind must be CMB3D_SPEC_PK or CMB3D_SPEC_CL");
   }
 
+  if (p->method == 2) return set_spectrum_2d(p, kn, pn, err, fit_err);
   // Eq. (2.11) for the cubic box: P_box(q) = P_inf(k_f sqrt q) k_f^3, k_f = 2 pi / L.
   const int N = p->N;
   const size_t nq = 3 * static_cast<size_t>(N / 2) * (N / 2) + 1;
@@ -1043,15 +1200,17 @@ int cmb3d_realize_sample_batch(const cmb3d_plan_t* plans, const uint64_t* seeds,
     int st = check_ready(plans[b]);
     if (st != CMB3D_OK) return st;
     if (plans[b]->N != plans[0]->N || plans[b]->L != plans[0]->L || plans[b]->interp != plans[0]->interp ||
-        plans[b]->device != plans[0]->device)
-      return fail(CMB3D_EINVAL, "batched plans must share N, L, interp and device");
+        plans[b]->device != plans[0]->device || plans[b]->method != plans[0]->method)
+      return fail(CMB3D_EINVAL, "batched plans must share the method, N, L, interp and device");
     if (plans[b]->npix > 0 && !outs_dev[b]) return fail(CMB3D_EINVAL, "outs_dev entry is NULL");
     for (int c = 0; c < b; ++c)
       if (plans[c] == plans[b]) return fail(CMB3D_EINVAL, "a plan appears twice in the batch (one box buffer each)");
   }
   DeviceGuard g(plans[0]->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (cmb3d::batch_supported(plans[0]->N)) {
+  bool all3d = true;
+  for (int b = 0; b < B; ++b) all3d = all3d && plans[b]->method == 3;
+  if (all3d && cmb3d::batch_supported(plans[0]->N)) {
     for (int b = 0; b < B; ++b)
       if (cudaError_t e = join_pipeline(plans[b], s); e != cudaSuccess) return fail_cuda(e, "pipeline join");
     int st = batch_run(plans, seeds, outs_dev, B, s);
@@ -1077,8 +1236,9 @@ int cmb3d_draw_spectrum(cmb3d_plan_t p, uint64_t seed, void* spec_dev, void* str
   if (st != CMB3D_OK) return st;
   if (!spec_dev) return fail(CMB3D_EINVAL, "spec_dev is NULL");
   DeviceGuard g(p->device);
-  cudaError_t e = cmb3d::launch_draw_only(p->N, static_cast<float2*>(spec_dev), p->amp, seed,
-                                          static_cast<cudaStream_t>(stream));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = p->method == 2 ? cmb3d::launch_draw2d(p->N, p->h, static_cast<float2*>(spec_dev), p->sqt, seed, s)
+                                 : cmb3d::launch_draw_only(p->N, static_cast<float2*>(spec_dev), p->amp, seed, s);
   if (e != cudaSuccess) return fail_cuda(e, "draw launch");
   return CMB3D_OK;
 }
@@ -1090,7 +1250,7 @@ int cmb3d_realize_field(cmb3d_plan_t p, uint64_t seed, float* field_dev, void* s
   DeviceGuard g(p->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if ((st = run_field(p, seed, s, false)) != CMB3D_OK) return st;
-  const size_t bytes = static_cast<size_t>(p->N) * p->N * p->N * sizeof(float);
+  const size_t bytes = static_cast<size_t>(p->method == 2 ? p->h : p->N) * p->N * p->N * sizeof(float);
   cudaError_t e = cudaMemcpyAsync(field_dev, p->buf, bytes, cudaMemcpyDeviceToDevice, s);
   if (e == cudaSuccess) e = mark_box0_used(p, s);
   if (e != cudaSuccess) return fail_cuda(e, "field copy");
@@ -1183,8 +1343,9 @@ int cmb3d_plan_info(cmb3d_plan_t p, int* N, int64_t* npix, int64_t* device_bytes
 
 int cmb3d_plan_prune_info(cmb3d_plan_t p, int64_t* planes, int64_t* rows) {
   if (!p) return fail(CMB3D_EINVAL, "plan is NULL");
-  if (planes) *planes = p->prune ? p->nplanes : p->N;
-  if (rows) *rows = p->prune ? p->nrows : static_cast<int64_t>(p->N) * p->N;
+  const int nz = p->method == 2 ? p->h : p->N;
+  if (planes) *planes = p->prune ? p->nplanes : nz;
+  if (rows) *rows = p->prune ? p->nrows : static_cast<int64_t>(nz) * p->N;
   return CMB3D_OK;
 }
 

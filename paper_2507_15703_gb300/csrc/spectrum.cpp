@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cmath>
 #include <limits>
+#include <thread>
 
 #include "cmb3d.h"
 
@@ -288,6 +289,94 @@ int fit_pk_from_cl(const double* ell, const double* cl, int n, int N, double L, 
   *pnodes = x;
   *max_rel_err = err;
   return CMB3D_OK;
+}
+
+void sqrt_symmetric(const double* a, int n, double* s) {
+  std::vector<double> A(a, a + static_cast<size_t>(n) * n), V(static_cast<size_t>(n) * n, 0.0);
+  for (int i = 0; i < n; ++i) V[static_cast<size_t>(i) * n + i] = 1.0;
+  auto at = [&](std::vector<double>& m, int i, int j) -> double& { return m[static_cast<size_t>(i) * n + j]; };
+  double fro = 0.0;
+  for (double x : A) fro += x * x;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0;
+    for (int i = 0; i < n; ++i)
+      for (int j = i + 1; j < n; ++j) off += 2.0 * at(A, i, j) * at(A, i, j);
+    if (off <= 1e-30 * fro) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const double apq = at(A, p, q);
+        if (apq == 0.0) continue;
+        // rotation angle zeroing A[p][q] (Golub & Van Loan, Alg. 8.4.1)
+        const double tau = (at(A, q, q) - at(A, p, p)) / (2.0 * apq);
+        const double t = (tau >= 0 ? 1.0 : -1.0) / (std::fabs(tau) + std::sqrt(1.0 + tau * tau));
+        const double c = 1.0 / std::sqrt(1.0 + t * t), sn = t * c;
+        for (int k = 0; k < n; ++k) {            // A <- A J (columns p, q)
+          const double akp = at(A, k, p), akq = at(A, k, q);
+          at(A, k, p) = c * akp - sn * akq;
+          at(A, k, q) = sn * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {            // A <- J^T A (rows p, q)
+          const double apk = at(A, p, k), aqk = at(A, q, k);
+          at(A, p, k) = c * apk - sn * aqk;
+          at(A, q, k) = sn * apk + c * aqk;
+        }
+        for (int k = 0; k < n; ++k) {            // V <- V J
+          const double vkp = at(V, k, p), vkq = at(V, k, q);
+          at(V, k, p) = c * vkp - sn * vkq;
+          at(V, k, q) = sn * vkp + c * vkq;
+        }
+      }
+  }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      double acc = 0.0;
+      for (int k = 0; k < n; ++k) acc += at(V, i, k) * std::sqrt(std::max(at(A, k, k), 0.0)) * at(V, j, k);
+      s[static_cast<size_t>(i) * n + j] = acc;
+    }
+}
+
+void sqrt_gamma_table(int N, int M, int h, double L, const std::vector<double>& knodes,
+                      const std::vector<double>& pnodes, int threads, std::vector<float>* table) {
+  const int H = N / 2;
+  const int nq = 2 * H * H + 1;
+  table->assign(static_cast<size_t>(nq) * h * h, 0.0f);
+  std::vector<char> reach(static_cast<size_t>(nq), 0);
+  for (int mx = 0; mx <= H; ++mx)
+    for (int f = -H + 1; f <= H; ++f) reach[static_cast<size_t>(mx * mx + f * f)] = 1;
+  const double dp = L / N;
+  const double kxy = 2.0 * M_PI / (N * dp), kz = 2.0 * M_PI / (M * dp);
+  const double vol = std::pow(2.0 * M_PI / dp, 3) / (static_cast<double>(M) * N * N);
+  // cos(2 pi m d / M) for m < M, d < h
+  std::vector<double> cs(static_cast<size_t>(M) * h);
+  for (int m = 0; m < M; ++m)
+    for (int d = 0; d < h; ++d)
+      cs[static_cast<size_t>(m) * h + d] = std::cos(2.0 * M_PI * static_cast<double>((static_cast<long long>(m) * d) % M) / M);
+  auto work = [&](int t) {
+    std::vector<double> col(static_cast<size_t>(M)), xi(static_cast<size_t>(h)), g(static_cast<size_t>(h) * h),
+        sq(static_cast<size_t>(h) * h);
+    for (int q = t; q < nq; q += threads) {
+      if (!reach[static_cast<size_t>(q)]) continue;
+      for (int m = 0; m < M; ++m) {
+        const int fz = m <= M / 2 ? m : m - M;
+        const double k = std::sqrt(kxy * kxy * q + kz * kz * static_cast<double>(fz) * fz);
+        col[static_cast<size_t>(m)] = (q == 0 && m == 0) ? 0.0 : pk_interp(knodes, pnodes, k) * vol;
+      }
+      for (int d = 0; d < h; ++d) {
+        double acc = 0.0;
+        for (int m = 0; m < M; ++m) acc += col[static_cast<size_t>(m)] * cs[static_cast<size_t>(m) * h + d];
+        xi[static_cast<size_t>(d)] = acc;
+      }
+      for (int i = 0; i < h; ++i)
+        for (int j = 0; j < h; ++j) g[static_cast<size_t>(i) * h + j] = xi[static_cast<size_t>(std::abs(i - j))];
+      sqrt_symmetric(g.data(), h, sq.data());
+      float* out = table->data() + static_cast<size_t>(q) * h * h;
+      for (int i = 0; i < h * h; ++i) out[i] = static_cast<float>(sq[static_cast<size_t>(i)]);
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int t = 1; t < threads; ++t) pool.emplace_back(work, t);
+  work(0);
+  for (auto& th : pool) th.join();
 }
 
 }  // namespace cmb3d

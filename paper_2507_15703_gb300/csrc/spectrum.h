@@ -33,4 +33,20 @@ std::vector<double> cl_design_matrix(const double* ell, int n, const std::vector
 int nnls(const std::vector<double>& A, int m, int n, const std::vector<double>& b, double ridge,
          std::vector<double>* x);
 
+// Symmetric square root S = V diag(sqrt(max(lambda, 0))) V^T of a symmetric
+// n x n matrix (row-major, FP64), by cyclic Jacobi rotations to convergence
+// (off-diagonal norm below 1e-15 of the Frobenius norm, or 100 sweeps).
+void sqrt_symmetric(const double* a, int n, double* s);
+
+// The 2-D Fourier method (paper Sec. II.D.2): for every q_perp = m_x^2 + m_y^2
+// in [0, 2 (N/2)^2] that the half plane m_x in [0, N/2], m_y signed in
+// (-N/2, N/2] reaches, the symmetric square root of the h x h covariance
+//   Gamma_ij = xi(|i - j| dp),  xi(d dp) = sum_{m_z} P_box(m) cos(2 pi m_z d / M),
+//   P_box(m) = P_inf(|k|) (2 pi / dp)^3 / (M N^2),  dp = L / N,
+//   k = (2 pi m_x/(N dp), 2 pi m_y/(N dp), 2 pi m_z/(M dp)),  P_box(0) = 0
+// (Eq. 2.11 with M != N), rounded to FP32: table[q][z][i], (2 (N/2)^2 + 1) x h x h.
+// Unreached q_perp are left zero.  Runs on `threads` host threads.
+void sqrt_gamma_table(int N, int M, int h, double L, const std::vector<double>& knodes,
+                      const std::vector<double>& pnodes, int threads, std::vector<float>* table);
+
 }  // namespace cmb3d

@@ -85,6 +85,17 @@ def batch_fsky(nbox: int, seed: int = 2507, lo: float = 0.05, hi: float = 0.5) -
     return np.random.default_rng(seed).uniform(lo, hi, nbox)
 
 
+def cap_layers(theta_max_deg: float, dp: float, r: float = 1.0, interp: int = 3) -> tuple[float, int]:
+    """Layers of the 2-D Fourier method that hold a polar cap of half-angle
+    theta_max on the sphere of radius r with grid step dp: layer 0 at
+    z0 = r cos(theta_max) - 1.5 dp (the cap's lowest pixels sit 1.5 steps up,
+    so a tricubic stencil keeps one layer below), and h layers up to the pole
+    with the stencil's margin above."""
+    z0 = r * math.cos(math.radians(theta_max_deg)) - 1.5 * dp
+    top = math.floor((r - z0) / dp)
+    return z0, top + (3 if interp == 3 else 2)
+
+
 @dataclasses.dataclass(frozen=True)
 class Workload:
     """A named synthetic workload: box, spectrum, pixels and interpolation."""
@@ -105,10 +116,18 @@ class Workload:
     learned: bool = False   # P(k) from the learned inversion (trained per run)
     n_train: int = 100000   # training spectra of the learned inversion
     train_seed: int = 4     # seed of the training and held-out spectra
+    method: str = "3d"      # "2d": the 2-D Fourier method on the cap's layers
+    M: int = 0              # 2-D: z-period in grid steps
+    theta_max_deg: float = 0.0   # 2-D: cap half-angle
+    dp: float = 0.0         # 2-D: grid step (box side L = N dp)
 
     @property
     def L(self) -> float:
-        return self.L_over_r * self.r
+        return self.N * self.dp if self.method == "2d" else self.L_over_r * self.r
+
+    def layers(self) -> tuple[float, int]:
+        """2-D: (z0, h) of the layers that hold the cap."""
+        return cap_layers(self.theta_max_deg, self.dp, self.r, self.interp)
 
     def pixels(self) -> np.ndarray:
         return cap_pixels(self.nside, self.fsky)
@@ -138,6 +157,14 @@ WORKLOADS = {
     # [800, 2000].
     "box2048_cap0.4_learned": Workload("box2048_cap0.4_learned", N=2048, nside=2048, fsky=0.4,
                                        lmax=2048, damping=1000.0, interp=3, nkbins=512, learned=True),
+    # 2-D Fourier method: a 20-degree polar cap (f_sky = (1 - cos 20 deg)/2,
+    # ~380k pixels of a 12*1024^2-point grid), N = 512 in x and y with step
+    # dp = 0.0034 r (the box spans 1.74 r, about twice the cap), z-period
+    # M = 64 and the 22 layers that hold the cap with a tricubic margin;
+    # the shape of the paper's Table I row (theta_max = 20 deg, N = 512, M = 64).
+    "fourier2d_box512_cap20": Workload("fourier2d_box512_cap20", N=512, nside=1024,
+                                       fsky=(1.0 - math.cos(math.radians(20.0))) / 2.0, lmax=768, damping=600.0,
+                                       interp=3, method="2d", M=64, theta_max_deg=20.0, dp=0.0034),
     # 1024^3 box, ~20M cap pixels, tricubic.
     "box1024_cap0.4_tricubic": Workload("box1024_cap0.4_tricubic", N=1024, nside=2048, fsky=0.4,
                                         lmax=768, damping=600.0, interp=3),

@@ -130,3 +130,34 @@ def test_product_and_oracle_are_independent():
     for f in os.listdir(os.path.join(ROOT, "oracle")):
         if f.endswith(".py"):
             assert "paper_2507_15703_gb300" not in _imports(os.path.join(ROOT, "oracle", f)), f
+
+
+@pytest.mark.parametrize("N,M,h", [(16, 16, 6), (32, 8, 12), (16, 64, 1), (32, 32, 32)])
+def test_gamma_sqrt_table_matches_oracle(lib, N, M, h):
+    """The 2-D method's per-q square roots (FP64 Jacobi in the library, numpy
+    eigh in the oracle) agree to FP32 rounding; unreached q stay zero."""
+    from oracle import fourier2d as f2
+    L = 2.2
+    k = np.linspace(0.0, np.sqrt(3) * np.pi * N / L, 64)
+    pk = 1e-3 / (1.0 + (k / 6.0) ** 3)
+    tab = cmb3d.cmb3d_gamma_sqrt_table(N, M, h, L, k, pk)
+    ref = f2.sqrt_gamma_table(N, M, h, L, k, pk)
+    for q in range(tab.shape[0]):
+        if q in ref:
+            assert np.max(np.abs(tab[q] - ref[q])) <= 1e-6 * np.max(np.abs(ref[q])), q
+        else:
+            assert not tab[q].any()
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(N=8), "CMB3D_EUNSUPPORTED"), (dict(h=33), "CMB3D_EUNSUPPORTED"), (dict(N=16, h=20), "CMB3D_EUNSUPPORTED"),
+    (dict(M=0), "CMB3D_EINVAL"), (dict(z0=float("nan")), "CMB3D_EINVAL"), (dict(L=0.0), "CMB3D_EINVAL"),
+    (dict(flags=1 << 4), "CMB3D_EUNSUPPORTED"), (dict(flags=1 << 6), "CMB3D_EUNSUPPORTED"),
+    (dict(flags=1 << 9), "CMB3D_EINVAL")])
+def test_plan_2d_rejects_bad_arguments(lib, kw, status):
+    args = dict(N=64, M=32, h=8, L=2.2, r=1.0, z0=0.5, flags=0)
+    args.update(kw)
+    with pytest.raises(cmb3d.Cmb3dError) as e:
+        cmb3d.cmb3d_plan_2d(args["N"], args["M"], args["h"], args["L"], args["r"], args["z0"], np.zeros((1, 3)), 3,
+                            args["flags"])
+    assert e.value.status == getattr(cmb3d, status)
