@@ -1,4 +1,5 @@
-"""Benchmark: partial-sky maps per second on the GB300 (3-D Fourier method).
+"""Benchmark: partial-sky maps per second on the GB300 (3-D Fourier method;
+the 2-D Fourier method with --workload fourier2d_box512_cap20).
 
 One step = one complete map of the workload through the C ABI: Philox draw
 fused with the z-FFT, y-FFT, x complex-to-real FFT and the tricubic gather at
@@ -175,16 +176,19 @@ def alu_peak_tinst(clk) -> tuple[float, str]:
     return sms * 128 * mhz * 1e6 / 1e12, f"derived: {sms} SMs x 4 schedulers x 32 lanes x {mhz:.0f} MHz"
 
 
-def algorithmic_bytes(N: int, npix: int, planes: int | None = None, rows: int | None = None) -> dict:
+def algorithmic_bytes(N: int, npix: int, planes: int | None = None, rows: int | None = None,
+                      nz: int | None = None) -> dict:
     """Bytes each kernel must move per launch (the packed half spectrum and the
-    real field are both 4 N^3 bytes, a row 4 N bytes): draw_zfft writes the
-    box once; yfft reads its z-planes and writes its rows; xc2r reads and
-    writes its rows; gather reads 16 B of table + 4 B of permutation per pixel
-    and writes 4 B per pixel (field reads are cache-dependent and not counted).
+    real field are both 4 N^2 nz bytes for nz z-planes, N for the 3-D box and
+    h layers for the 2-D method; a row is 4 N bytes): the draw writes the box
+    once; yfft reads its z-planes and writes its rows; xc2r reads and writes
+    its rows; gather reads 16 B of table + 4 B of permutation per pixel and
+    writes 4 B per pixel (field reads are cache-dependent and not counted).
     planes, rows: the pruned extent of the sky-map path (default: whole box)."""
-    box, row = 4 * N ** 3, 4 * N
-    planes = N if planes is None else planes
-    rows = N * N if rows is None else rows
+    nz = N if nz is None else nz
+    box, row = 4 * N * N * nz, 4 * N
+    planes = nz if planes is None else planes
+    rows = nz * N if rows is None else rows
     return {"draw_zfft": box, "yfft": planes * N * row + rows * row, "xc2r": 2 * rows * row,
             "gather": 24 * npix, "yx_fused": 2 * box}
 
@@ -221,7 +225,13 @@ def run_cuda(args, rank, world, local):
         flags |= cmb3d.CMB3D_FLAG_PIPELINE
     if args.schedule:
         flags &= ~cmb3d.CMB3D_FLAG_AUTOTUNE
-    plan = cmb3d.Plan(w.N, w.L, w.r, pix, w.interp, flags)
+    if w.method == "2d":
+        z0, nlayers = w.layers()
+        make = lambda fl: cmb3d.Plan2D(w.N, w.M, nlayers, w.L, w.r, z0, pix, w.interp, fl)   # noqa: E731
+    else:
+        nlayers = w.N
+        make = lambda fl: cmb3d.Plan(w.N, w.L, w.r, pix, w.interp, fl)   # noqa: E731
+    plan = make(flags)
     if args.schedule:
         cmb3d.cmb3d_plan_set_schedule(plan.handle, tuple(int(v) for v in args.schedule.split(",")))
     if learned is not None:
@@ -292,7 +302,7 @@ def run_cuda(args, rank, world, local):
         # the same maps through a pipelined plan (second box, draw of map i+1
         # overlapping the passes and gather of map i); CUDA events, same stream
         pflags = (flags | cmb3d.CMB3D_FLAG_PIPELINE) & ~cmb3d.CMB3D_FLAG_STAGE_TIMING & ~cmb3d.CMB3D_FLAG_AUTOTUNE
-        pplan = cmb3d.Plan(w.N, w.L, w.r, pix, w.interp, pflags)
+        pplan = make(pflags)
         cmb3d.cmb3d_plan_set_schedule(pplan.handle, schedule)
         pplan.set_pk(*plan_pk)
         for i in range(args.warmup):
@@ -317,7 +327,7 @@ def run_cuda(args, rank, world, local):
 
     maps = world * args.steps
     value = job_throughput(world, args.steps, t_max)
-    ab = algorithmic_bytes(w.N, npix, n_planes, n_rows)
+    ab = algorithmic_bytes(w.N, npix, n_planes, n_rows, nlayers)
     names = cmb3d.STAGE_NAMES
     kernels = {}
     for i, name in enumerate(names):
@@ -327,7 +337,7 @@ def run_cuda(args, rank, world, local):
         kernels[name] = kernel_entry(n, stage_ms[i], stage_ms.sum(), ab[name])
     dom = names[int(np.argmax(stage_ms))]
     per_map_bytes = sum(ab[k] for k in kernels)
-    config = {"workload": args.workload, "N": w.N, "L_over_r": w.L_over_r, "npix": npix, "fsky": w.fsky,
+    config = {"workload": args.workload, "N": w.N, "L_over_r": round(w.L / w.r, 4), "npix": npix, "fsky": w.fsky,
               "interp": "tricubic" if w.interp == 3 else "trilinear", "lmax": w.lmax, "nkbins": w.nkbins,
               "parallelism": f"replicas x{world}",
               "schedule": {"draw": schedule[0], "y": schedule[1], "x": schedule[2], "fused_yx": schedule[3],
@@ -339,6 +349,9 @@ def run_cuda(args, rank, world, local):
                                            "interpolation stencils read; maps equal the whole-box maps bit for bit"},
               "l2": f"no flush: per-map working set {per_map_bytes / 2**30:.2f} GiB > 129 MiB L2",
               "cl_fit_max_rel_err": fit_err, "plan_setup_s": round(setup_s, 2),
+              "method": ({"name": "2-D Fourier method (Sec. II.D.2)", "M": w.M, "h": nlayers,
+                          "z0": round(z0, 6), "dp": w.dp, "theta_max_deg": w.theta_max_deg}
+                         if w.method == "2d" else {"name": "3-D Fourier method (Sec. II.D.1)"}),
               "pipelined_plan": pipe_info,
               "e2e_d2h_ms_per_map": round(d2h_ms, 4),
               "e2e_d2h_gbs": round(4 * npix / (d2h_ms / 1e3) / 1e9, 1)}

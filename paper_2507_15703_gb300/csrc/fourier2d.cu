@@ -19,87 +19,77 @@ namespace cmb3d {
 namespace {
 
 constexpr float kRsqrt2 = 0.70710678118654752f;
+constexpr int kWarps = 8, kTile = 32;                 // 8 warps per block; up to 32 modes (m_x') per block
 
-// Normals of mode (mx, my): c[i] = (g1 + i g2) / sqrt 2, or (g1, 0) when real.
-template <int HM>
-__device__ __forceinline__ void mode_normals(int mx, int my, int h, uint2 key, bool real, float2 (&c)[HM]) {
-#pragma unroll
-  for (int ip = 0; ip < HM / 2; ++ip) {
-    if (2 * ip < h) {
-      const uint4 w = philox4x32_10(make_uint4(mx, my, ip, 1u), key);
-      const float2 ga = box_muller(w.x, w.y), gb = box_muller(w.z, w.w);
-      c[2 * ip] = real ? make_float2(ga.x, 0.f) : make_float2(ga.x * kRsqrt2, ga.y * kRsqrt2);
-      c[2 * ip + 1] = real ? make_float2(gb.x, 0.f) : make_float2(gb.x * kRsqrt2, gb.y * kRsqrt2);
-    }
-  }
-}
-
-// Row z of S times c (complex vector, real matrix).
-template <int HM>
-__device__ __forceinline__ float2 row_times(const float* __restrict__ S, int z, int h, const float2 (&c)[HM]) {
-  float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-  for (int i = 0; i < HM; ++i) {
-    if (i < h) {
-      const float sz = __ldg(S + z * h + i);
-      acc.x = fmaf(sz, c[i].x, acc.x);
-      acc.y = fmaf(sz, c[i].y, acc.y);
-    }
-  }
-  return acc;
-}
-
-// The h values of a mode on a Hermitian line m_x in {0, N/2}, into v.
-template <int HM>
-__device__ __forceinline__ void hermitian_mode(int mx, int my, int N, int h, const float* __restrict__ tab,
-                                               uint2 key, float2 (&v)[HM]) {
+// Layer values of one mode, computed by a warp: lane z < h returns
+// T^(mx, my, z).  The mode's h x h factor is staged in shared memory (rows of
+// h + 1 floats: lane z reads row z without bank conflicts) and its normals in
+// sc[h]; lanes ip < (h + 1)/2 draw the Philox block (mx, my', ip, 1).
+// On a Hermitian line (mx in {0, N/2}) the partner of a drawing mode takes the
+// conjugate of the drawing mode's values and self-conjugate modes are real.
+__device__ __forceinline__ float2 warp_mode(int mx, int my, int N, int h, const float* __restrict__ tab, uint2 key,
+                                            float* sS, float2* sc, int lane) {
+  const bool line = mx == 0 || mx == N / 2;
   const int py = (N - my) & (N - 1);
+  const bool self = line && py == my, partner = line && !self && py < my;
   const int fy = my <= N / 2 ? my : my - N;
   const float* S = tab + static_cast<size_t>(mx * mx + fy * fy) * h * h;
-  float2 c[HM];
-  const bool self = py == my, own = my < py;
-  mode_normals<HM>(mx, self || own ? my : py, h, key, self, c);
-#pragma unroll
-  for (int z = 0; z < HM; ++z) {
-    if (z < h) {
-      const float2 a = row_times<HM>(S, z, h, c);
-      v[z] = own || self ? a : make_float2(a.x, -a.y);
+#pragma unroll 8
+  for (int e = lane; e < h * h; e += 32) {          // loads of several iterations in flight
+    const int z = e / h;
+    sS[z * (h + 1) + (e - z * h)] = __ldg(S + e);
+  }
+  if (2 * lane < h) {
+    const uint4 w = philox4x32_10(make_uint4(mx, partner ? py : my, lane, 1u), key);
+    const float2 ga = box_muller(w.x, w.y), gb = box_muller(w.z, w.w);
+    sc[2 * lane] = self ? make_float2(ga.x, 0.f) : make_float2(ga.x * kRsqrt2, ga.y * kRsqrt2);
+    if (2 * lane + 1 < h) sc[2 * lane + 1] = self ? make_float2(gb.x, 0.f) : make_float2(gb.x * kRsqrt2, gb.y * kRsqrt2);
+  }
+  __syncwarp();
+  float2 acc = make_float2(0.f, 0.f);
+  if (lane < h) {
+    const float* row = sS + lane * (h + 1);
+#pragma unroll 8
+    for (int i = 0; i < h; ++i) {                    // one accumulator, i ascending; loads run ahead
+      const float si = row[i];
+      acc.x = fmaf(si, sc[i].x, acc.x);
+      acc.y = fmaf(si, sc[i].y, acc.y);
     }
   }
+  __syncwarp();                                      // staging is reused by the warp's next mode
+  return partner ? make_float2(acc.x, -acc.y) : acc;
 }
 
-template <int HM>
-__global__ void __launch_bounds__(256) k_draw2d(float2* __restrict__ buf, const float* __restrict__ tab, int N,
-                                                int h, uint2 key) {
-  const int N2 = N / 2;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= N2 * N) return;
-  const int xp = t % N2, my = t / N2;
-  float2* out = buf + static_cast<size_t>(my) * N2 + xp;       // (z, my, xp) at out[z N N2]
-  const size_t plane = static_cast<size_t>(N) * N2;
-  if (xp > 0) {
-    const int fy = my <= N2 ? my : my - N;
-    const float* S = tab + static_cast<size_t>(xp * xp + fy * fy) * h * h;
-    float2 c[HM];
-    mode_normals<HM>(xp, my, h, key, false, c);
-#pragma unroll
-    for (int z = 0; z < HM; ++z)
-      if (z < h) out[z * plane] = row_times<HM>(S, z, h, c);
-    return;
+// Block (m_x' tile blockIdx.x, m_y = blockIdx.y): its warps take the tile's
+// modes in turn; the layers go through shared memory [z][mode] so each layer
+// is stored as one row of consecutive m_x'.
+__global__ void __launch_bounds__(kWarps * 32) k_draw2d(float2* __restrict__ buf, const float* __restrict__ tab,
+                                                        int N, int h, uint2 key) {
+  extern __shared__ float smem[];
+  const int N2 = N / 2, tw = N2 < kTile ? N2 : kTile;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int xp0 = blockIdx.x * tw, my = blockIdx.y;
+  float2* sout = reinterpret_cast<float2*>(smem);                          // [h][kTile]
+  float* region = smem + 2 * h * kTile + warp * (h * (h + 3));             // per warp: sc[h], then sS[h][h + 1]
+  float2* sc = reinterpret_cast<float2*>(region);
+  float* sS = region + 2 * h;
+  for (int m = warp; m < tw; m += kWarps) {
+    const int xp = xp0 + m;
+    float2 v;
+    if (xp == 0) {                                   // slot 0 packs T^(0, .) + i T^(N/2, .)
+      const float2 a = warp_mode(0, my, N, h, tab, key, sS, sc, lane);
+      const float2 b = warp_mode(N2, my, N, h, tab, key, sS, sc, lane);
+      v = make_float2(a.x - b.y, a.y + b.x);
+    } else {
+      v = warp_mode(xp, my, N, h, tab, key, sS, sc, lane);
+    }
+    if (lane < h) sout[lane * kTile + m] = v;
   }
-  float2 a[HM], b[HM];
-  hermitian_mode<HM>(0, my, N, h, tab, key, a);
-  hermitian_mode<HM>(N2, my, N, h, tab, key, b);
-#pragma unroll
-  for (int z = 0; z < HM; ++z)
-    if (z < h) out[z * plane] = make_float2(a[z].x - b[z].y, a[z].y + b[z].x);
-}
-
-template <int HM>
-cudaError_t run_draw2d(int N, int h, float2* buf, const float* tab, uint2 key, cudaStream_t s) {
-  const int n = N / 2 * N;
-  k_draw2d<HM><<<(n + 255) / 256, 256, 0, s>>>(buf, tab, N, h, key);
-  return cudaGetLastError();
+  __syncthreads();
+  for (int e = threadIdx.x; e < h * tw; e += kWarps * 32) {
+    const int z = e / tw, m = e - z * tw;
+    buf[(static_cast<size_t>(z) * N + my) * N2 + xp0 + m] = sout[z * kTile + m];
+  }
 }
 
 }  // namespace
@@ -107,9 +97,12 @@ cudaError_t run_draw2d(int N, int h, float2* buf, const float* tab, uint2 key, c
 cudaError_t launch_draw2d(int N, int h, float2* buf, const float* tab, uint64_t seed, cudaStream_t s) {
   if (N < 16 || (N & (N - 1)) || h < 1 || h > 32) return cudaErrorInvalidValue;
   const uint2 key = make_uint2(static_cast<uint32_t>(seed & 0xFFFFFFFFu), static_cast<uint32_t>(seed >> 32));
-  if (h <= 8) return run_draw2d<8>(N, h, buf, tab, key, s);
-  if (h <= 16) return run_draw2d<16>(N, h, buf, tab, key, s);
-  return run_draw2d<32>(N, h, buf, tab, key, s);
+  const int N2 = N / 2, tw = N2 < kTile ? N2 : kTile;
+  const size_t smem = sizeof(float) * (2 * h * kTile + kWarps * h * (h + 3));
+  cudaError_t e = cudaFuncSetAttribute(k_draw2d, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  k_draw2d<<<dim3(N2 / tw, N), kWarps * 32, smem, s>>>(buf, tab, N, h, key);
+  return cudaGetLastError();
 }
 
 }  // namespace cmb3d
