@@ -34,10 +34,9 @@ __device__ __forceinline__ float2 warp_mode(int mx, int my, int N, int h, const 
   const bool self = line && py == my, partner = line && !self && py < my;
   const int fy = my <= N / 2 ? my : my - N;
   const float* S = tab + static_cast<size_t>(mx * mx + fy * fy) * h * h;
+  if (lane < h) {                                   // row by row: lane i copies column i
 #pragma unroll 8
-  for (int e = lane; e < h * h; e += 32) {          // loads of several iterations in flight
-    const int z = e / h;
-    sS[z * (h + 1) + (e - z * h)] = __ldg(S + e);
+    for (int z = 0; z < h; ++z) sS[z * (h + 1) + lane] = __ldg(S + z * h + lane);
   }
   if (2 * lane < h) {
     const uint4 w = philox4x32_10(make_uint4(mx, partner ? py : my, lane, 1u), key);
