@@ -141,6 +141,9 @@ KERNEL_SOURCES = {
     "gather": ["paper_2507_15703_gb300/csrc/gather.cu", "paper_2507_15703_gb300/csrc/gather_tiles.cuh"],
     "batch": ["paper_2507_15703_gb300/csrc/batch.cu", "paper_2507_15703_gb300/csrc/fft_tiles.cuh"],
 }
+# the 2-D Fourier method draws with its own kernel
+KERNEL_SOURCES_2D = dict(KERNEL_SOURCES, draw_zfft=["paper_2507_15703_gb300/csrc/fourier2d.cu",
+                                                    "paper_2507_15703_gb300/csrc/device_common.cuh"])
 # kernels whose limiter is instruction issue, not HBM (the draw: Philox,
 # Box-Muller and the first FFT stages for every mode, one write of the box)
 ALU_BOUND = {"draw_zfft"}
@@ -151,12 +154,13 @@ def ncu_counters(kernel: str, workload: str):
     (dram_bytes_per_launch, thread_inst_per_launch), or None when the kernel
     source changed since they were taken."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
-    if not os.path.exists(p) or kernel not in KERNEL_SOURCES:
+    srcs = KERNEL_SOURCES_2D if workload in WORKLOADS and WORKLOADS[workload].method == "2d" else KERNEL_SOURCES
+    if not os.path.exists(p) or kernel not in srcs:
         return None
     with open(p) as f:
         d = json.load(f)
     e = d.get(workload, {}).get(kernel)
-    if not e or e.get("source_hash") != source_hash(KERNEL_SOURCES[kernel]):
+    if not e or e.get("source_hash") != source_hash(srcs[kernel]):
         return None
     return e
 
