@@ -195,8 +195,12 @@ int cmb3d_gamma_sqrt_table(int N, int M, int h, double L, const double* k, const
  *     relative error of the forward-projected C_l.
  * Then P_box(q) = P_inf(2 pi sqrt(q) / L) (2 pi / L)^3 (Eq. 2.11 with M = N)
  * is tabulated for q = 0 .. 3 (N/2)^2 and the table sqrt(P_box / 2) is
- * uploaded (one synchronous host-to-device copy).
- * Errors: CMB3D_EINVAL for bad arrays, CMB3D_ECUDA for the upload.
+ * uploaded (one synchronous host-to-device copy).  On a plan of the 2-D
+ * method (cmb3d_plan_2d) the uploaded table is instead the factor table of
+ * cmb3d_gamma_sqrt_table for the plan's N, M, h and L ((2 (N/2)^2 + 1) h^2
+ * floats, built on the host cores).
+ * Errors: CMB3D_EINVAL for bad arrays, CMB3D_ENOMEM if the host table cannot
+ * be allocated, CMB3D_ECUDA for the upload.
  */
 int cmb3d_set_spectrum(cmb3d_plan_t plan, int kind, const double* x, const double* y,
                        int n, int nkbins, double* fit_err);
