@@ -232,6 +232,62 @@ int cmb3d_fit_pk(const double* ell, const double* cl, int n, int N, double L, do
 int cmb3d_cl_matrix(const double* ell, int n, const double* knodes, int nk, double r, double* out);
 
 /*
+ * The paper's linear-programming inversion (Sec. II.B), host only, needing no
+ * GPU.  It finds P_inf >= 0 whose flat-space correlation function
+ * xi_inf(r) = 4 pi int k P(k) sin(k r)/r dk (Eq. 2.4) matches the sphere's
+ * xi_sph(theta) = sum_l (2l+1) C_l exp(-beam^2 l^2) P_l(cos theta) / (4 pi)
+ * (Eq. 2.1 with the smoothing of Eq. 2.2) at the chords r = 2 R sin(theta/2)
+ * (Eq. 2.3) of every separation in a polar cap of half-angle theta_max.
+ *
+ * Discretisation:
+ *   - separations r_i = i dr, i < m = floor(r_max / dr) + 1, with r_max =
+ *     2 R sin(theta_max) for theta_max <= pi/2 and 2 R beyond (the largest
+ *     chord in the cap); targets b_i = xi_sph(theta_i), cos theta_i =
+ *     1 - r_i^2 / (2 R^2);
+ *   - unknowns x_j = P_inf(k_j) at k_j = j dk, j < nk = floor(kmax / dk);
+ *     P_inf is linear between nodes and zero from k_nk = nk dk on, so the
+ *     result is nk + 1 nodes whose last value is 0;
+ *   - A_ij = 4 pi int k phi_j(k) sin(k r_i)/r_i dk (k^2 at r = 0), phi_j the
+ *     hat function of node j, by Gauss-Legendre (16 points per interval).
+ * The program (Eq. 2.5): minimise c^T x with c_j = sum_i A_ij subject to
+ * A x >= b and x >= 0; its minimum is sum_i b_i exactly when A x = b has a
+ * solution x >= 0.  Solved by a dense two-phase simplex on the dual problem
+ * (n rows) in FP64.
+ *
+ *   ell, cl      host arrays of n multipoles (integers in [0, 100000],
+ *                increasing) and C_l >= 0 (unsmoothed; beam is applied).
+ *   R            sphere radius, > 0.
+ *   theta_max    polar half-angle of the cap in radians, (0, pi].
+ *   beam         Gaussian beam width b in radians (>= 0; 0 = no smoothing).
+ *   dr, dk       separation and node steps; dr = 0 selects beam / 5 (then
+ *                beam must be > 0) and dk = 0 selects 2 pi / (3 r_max), the
+ *                paper's defaults.
+ *   kmax         P_inf is zero above kmax (>= dk), e.g. sqrt(3) pi N / L, the
+ *                largest |k| of a box.
+ *
+ * cmb3d_lp_system reports the program without solving it: m_out, nk_out
+ * receive m and nk; each of r_out (m doubles), knodes_out (nk + 1), A_out
+ * (m x nk, row-major) and b_out (m) may be NULL and is filled otherwise.
+ *
+ * cmb3d_fit_pk_lp solves it: knodes_out and pk_out (cap >= nk + 1 doubles
+ * each) receive the nodes and P_inf at them, nk_out the count nk + 1;
+ * objective (may be NULL) receives c^T x and xi_err (may be NULL)
+ * max_i |(A x)_i - b_i| / |b_0|.  The result feeds
+ * cmb3d_set_spectrum(CMB3D_SPEC_PK) unchanged.
+ *
+ * Errors: CMB3D_EINVAL for bad arguments or a too small cap;
+ * CMB3D_EUNSUPPORTED above 1e6 separations, 1e5 nodes or 6.4e7 matrix or
+ * tableau entries, or if the simplex reaches its pivot limit
+ * (100 (m + nk) + 10000); CMB3D_ENOMEM if host memory runs out.
+ */
+int cmb3d_lp_system(const double* ell, const double* cl, int n, double R, double theta_max, double beam,
+                    double dr, double dk, double kmax, int* m_out, int* nk_out, double* r_out,
+                    double* knodes_out, double* A_out, double* b_out);
+int cmb3d_fit_pk_lp(const double* ell, const double* cl, int n, double R, double theta_max, double beam,
+                    double dr, double dk, double kmax, int cap, double* knodes_out, double* pk_out,
+                    int* nk_out, double* objective, double* xi_err);
+
+/*
  * Read back the plan's fitted P_inf(k) at n points (paper Sec. II.B output).
  *   k   host pointer, n abscissae (input); pk host pointer, n values (output).
  * Returns CMB3D_ENOSPEC before cmb3d_set_spectrum.

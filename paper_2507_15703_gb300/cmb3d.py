@@ -63,6 +63,10 @@ PROTOTYPES = {
     "cmb3d_gamma_sqrt_table": (_i32, [_i32, _i32, _i32, C.c_double, _dp, _dp, _i32, C.POINTER(C.c_float)]),
     "cmb3d_set_spectrum": (_i32, [_vp, _i32, _dp, _dp, _i32, _i32, _dp]),
     "cmb3d_fit_pk": (_i32, [_dp, _dp, _i32, _i32, C.c_double, C.c_double, _i32, _dp, _dp, _dp]),
+    "cmb3d_lp_system": (_i32, [_dp, _dp, _i32, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
+                               C.c_double, C.POINTER(_i32), C.POINTER(_i32), _dp, _dp, _dp, _dp]),
+    "cmb3d_fit_pk_lp": (_i32, [_dp, _dp, _i32, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
+                               C.c_double, _i32, _dp, _dp, C.POINTER(_i32), _dp, _dp]),
     "cmb3d_get_pk": (_i32, [_vp, _dp, _dp, _i32]),
     "cmb3d_cl_matrix": (_i32, [_dp, _i32, _dp, _i32, C.c_double, _dp]),
     "cmb3d_realize_sample": (_i32, [_vp, _u64, _vp, _vp]),
@@ -216,6 +220,45 @@ def cmb3d_fit_pk(ell, cl, N: int, L: float, r: float, nk: int = 256):
     _check(lib.cmb3d_fit_pk(ea.ctypes.data_as(_dp), ca.ctypes.data_as(_dp), ea.size, int(N), float(L), float(r),
                             int(nk), kn.ctypes.data_as(_dp), pk.ctypes.data_as(_dp), C.byref(err)), "cmb3d_fit_pk")
     return kn, pk, err.value
+
+
+def _lp_args(ell, cl, R, theta_max, beam, dr, dk, kmax):
+    ea, ca = _f64(ell), _f64(cl)
+    if ea.shape != ca.shape or ea.ndim != 1:
+        raise ValueError("ell and cl must be 1-D arrays of equal length")
+    return (ea, ca, (ea.ctypes.data_as(_dp), ca.ctypes.data_as(_dp), ea.size, float(R), float(theta_max),
+                     float(beam), float(dr), float(dk), float(kmax)))
+
+
+def cmb3d_lp_system(ell, cl, R: float, theta_max: float, beam: float = 0.0, dr: float = 0.0, dk: float = 0.0,
+                    kmax: float = 0.0):
+    """The linear program of the paper's inversion (Sec. II.B) without solving
+    it: (r [m], knodes [nk + 1], A [m, nk], b [m])."""
+    lib = load()
+    ea, ca, head = _lp_args(ell, cl, R, theta_max, beam, dr, dk, kmax)
+    m, nk = _i32(0), _i32(0)
+    _check(lib.cmb3d_lp_system(*head, C.byref(m), C.byref(nk), None, None, None, None), "cmb3d_lp_system")
+    r, kn = np.empty(m.value), np.empty(nk.value + 1)
+    A, b = np.empty((m.value, nk.value)), np.empty(m.value)
+    _check(lib.cmb3d_lp_system(*head, C.byref(m), C.byref(nk), r.ctypes.data_as(_dp), kn.ctypes.data_as(_dp),
+                               A.ctypes.data_as(_dp), b.ctypes.data_as(_dp)), "cmb3d_lp_system")
+    return r, kn, A, b
+
+
+def cmb3d_fit_pk_lp(ell, cl, R: float, theta_max: float, beam: float = 0.0, dr: float = 0.0, dk: float = 0.0,
+                    kmax: float = 0.0):
+    """The paper's LP inversion (Sec. II.B), host only: returns (knodes, pk,
+    objective c^T x, max |A x - b| / |b_0|)."""
+    lib = load()
+    ea, ca, head = _lp_args(ell, cl, R, theta_max, beam, dr, dk, kmax)
+    m, nk = _i32(0), _i32(0)
+    _check(lib.cmb3d_lp_system(*head, C.byref(m), C.byref(nk), None, None, None, None), "cmb3d_lp_system")
+    cap = nk.value + 1
+    kn, pk = np.empty(cap), np.empty(cap)
+    obj, err, cnt = C.c_double(0.0), C.c_double(0.0), _i32(0)
+    _check(lib.cmb3d_fit_pk_lp(*head, cap, kn.ctypes.data_as(_dp), pk.ctypes.data_as(_dp), C.byref(cnt),
+                               C.byref(obj), C.byref(err)), "cmb3d_fit_pk_lp")
+    return kn[:cnt.value], pk[:cnt.value], obj.value, err.value
 
 
 def cmb3d_cl_matrix(ell, knodes, r: float) -> np.ndarray:

@@ -830,6 +830,93 @@ int cmb3d_cl_matrix(const double* ell, int n, const double* knodes, int nk, doub
   return CMB3D_OK;
 }
 
+// The linear-programming inversion (paper Sec. II.B): argument checks, the
+// grid, the targets and the matrix, shared by the two entry points below.
+namespace {
+
+int lp_setup(const double* ell, const double* cl, int nl, double R, double theta_max, double beam, double dr,
+             double dk, double kmax, cmb3d::LpGrid* g, std::vector<double>* b, std::vector<double>* A) {
+  if (!ell || !cl || nl < 1) return fail(CMB3D_EINVAL, "ell, cl must be non-NULL with n >= 1");
+  for (int i = 0; i < nl; ++i) {
+    if (!std::isfinite(ell[i]) || ell[i] < 0 || ell[i] != std::floor(ell[i]) || ell[i] > 100000 ||
+        !std::isfinite(cl[i]) || cl[i] < 0)
+      return fail(CMB3D_EINVAL, "l must be integers in [0, 100000] and C_l finite and >= 0");
+    if (i > 0 && !(ell[i] > ell[i - 1])) return fail(CMB3D_EINVAL, "l must be strictly increasing");
+  }
+  int st = cmb3d::lp_grid(R, theta_max, beam, dr, dk, kmax, g, &g_detail);
+  if (st != CMB3D_OK) return st;
+  if (static_cast<double>(g->m) * g->n > 6.4e7 || static_cast<double>(g->n) * (g->m + 2.0 * g->n) > 6.4e7)
+    return fail(CMB3D_EUNSUPPORTED, "linear program larger than 6.4e7 matrix or tableau entries");
+  try {
+    cmb3d::lp_targets(ell, cl, nl, beam, R, *g, b);
+    if (A) {
+      const unsigned hc = std::thread::hardware_concurrency();
+      cmb3d::lp_matrix(*g, static_cast<int>(std::max(1u, std::min(hc, 32u))), A);
+    }
+  } catch (const std::bad_alloc&) {
+    return fail(CMB3D_ENOMEM, "host allocation of the linear program");
+  }
+  return CMB3D_OK;
+}
+
+}  // namespace
+
+int cmb3d_lp_system(const double* ell, const double* cl, int n, double R, double theta_max, double beam,
+                    double dr, double dk, double kmax, int* m_out, int* nk_out, double* r_out, double* knodes_out,
+                    double* A_out, double* b_out) {
+  if (!m_out || !nk_out) return fail(CMB3D_EINVAL, "m_out and nk_out must be non-NULL");
+  cmb3d::LpGrid g;
+  std::vector<double> b, A;
+  int st = lp_setup(ell, cl, n, R, theta_max, beam, dr, dk, kmax, &g, &b, A_out ? &A : nullptr);
+  if (st != CMB3D_OK) return st;
+  *m_out = g.m;
+  *nk_out = g.n;
+  if (r_out)
+    for (int i = 0; i < g.m; ++i) r_out[i] = i * g.dr;
+  if (knodes_out)
+    for (int j = 0; j <= g.n; ++j) knodes_out[j] = j * g.dk;
+  if (b_out) std::copy(b.begin(), b.end(), b_out);
+  if (A_out) std::copy(A.begin(), A.end(), A_out);
+  return CMB3D_OK;
+}
+
+int cmb3d_fit_pk_lp(const double* ell, const double* cl, int n, double R, double theta_max, double beam,
+                    double dr, double dk, double kmax, int cap, double* knodes_out, double* pk_out, int* nk_out,
+                    double* objective, double* xi_err) {
+  if (!knodes_out || !pk_out || !nk_out) return fail(CMB3D_EINVAL, "output arrays are NULL");
+  cmb3d::LpGrid g;
+  std::vector<double> b, A, x;
+  int st = lp_setup(ell, cl, n, R, theta_max, beam, dr, dk, kmax, &g, &b, &A);
+  if (st != CMB3D_OK) return st;
+  if (cap < g.n + 1) return fail(CMB3D_EINVAL, "cap is smaller than the number of k nodes (nk + 1)");
+  long pivots = 0;
+  try {
+    st = cmb3d::lp_solve(A, g.m, g.n, b, 100L * (g.m + g.n) + 10000, &x, &pivots, &g_detail);
+  } catch (const std::bad_alloc&) {
+    return fail(CMB3D_ENOMEM, "host allocation of the simplex tableau");
+  }
+  if (st != CMB3D_OK) return st;
+  double obj = 0.0, worst = 0.0;
+  for (int j = 0; j < g.n; ++j) {
+    double c = 0.0;
+    for (int i = 0; i < g.m; ++i) c += A[static_cast<size_t>(i) * g.n + j];
+    obj += c * x[static_cast<size_t>(j)];
+  }
+  for (int i = 0; i < g.m; ++i) {
+    double s = 0.0;
+    for (int j = 0; j < g.n; ++j) s += A[static_cast<size_t>(i) * g.n + j] * x[static_cast<size_t>(j)];
+    worst = std::max(worst, std::fabs(s - b[static_cast<size_t>(i)]));
+  }
+  for (int j = 0; j <= g.n; ++j) {
+    knodes_out[j] = j * g.dk;
+    pk_out[j] = j < g.n ? x[static_cast<size_t>(j)] : 0.0;
+  }
+  *nk_out = g.n + 1;
+  if (objective) *objective = obj;
+  if (xi_err) *xi_err = b[0] != 0.0 ? worst / std::fabs(b[0]) : worst;
+  return CMB3D_OK;
+}
+
 // The 2-D method's per-q square roots of the z-covariance (host FP64, then
 // FP32 on the device) from P_inf on the nodes (kn, pn).
 static int set_spectrum_2d(cmb3d_plan_s* p, std::vector<double>& kn, std::vector<double>& pn, double err,

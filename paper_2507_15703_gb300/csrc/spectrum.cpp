@@ -30,8 +30,6 @@ double pk_interp(const std::vector<double>& k, const std::vector<double>& p, dou
   return p[i - 1] + t * (p[i] - p[i - 1]);
 }
 
-namespace {
-
 // Gauss-Legendre nodes and weights on [-1, 1] by Newton iteration on P_n.
 void gauss_legendre(int n, std::vector<double>* x, std::vector<double>* w) {
   x->assign(static_cast<size_t>(n), 0.0);
@@ -58,6 +56,8 @@ void gauss_legendre(int n, std::vector<double>* x, std::vector<double>* w) {
     (*w)[static_cast<size_t>(n - 1 - i)] = wi;
   }
 }
+
+namespace {
 
 // j_l(x)^2 for l = 0..lmax by Miller's downward recurrence
 // j_{l-1} = (2l+1)/x j_l - j_{l+1}, started well above max(lmax, x) and
