@@ -316,6 +316,25 @@ int cmb3d_realize_sample_to_host(cmb3d_plan_t plan, uint64_t seed, float* out_ho
                                  void* stream);
 
 /*
+ * `count` maps delivered to host memory in one call, map i of realization
+ * seeds[i] into outs_host[i] (npix floats each, the caller's pixel order).
+ * The maps are computed in order on `stream` into two device staging buffers
+ * used in turn; each map's download runs on a copy stream of the plan while
+ * the kernels of the next map run, so with page-locked (pinned) host buffers
+ * the copies overlap the computation.  Pageable host memory works but makes
+ * each copy blocking.  Returns when every copy has completed (synchronises
+ * `stream`).  The same host pointer may appear more than once; it then holds
+ * the last of its maps.  The second staging buffer (4 npix bytes) and the
+ * copy stream are created on the first call and kept by the plan.
+ *   seeds      host array of count seeds; outs_host host array of count
+ *              pointers.  count = 0 does nothing.
+ * Errors: as cmb3d_realize_sample_to_host; CMB3D_EINVAL for NULL arrays or
+ * a NULL output pointer with npix > 0.
+ */
+int cmb3d_realize_samples_to_host(cmb3d_plan_t plan, const uint64_t* seeds, int count, float* const* outs_host,
+                                  void* stream);
+
+/*
  * Many maps at once (batched form of Sec. II.D.1; the paper generates batches
  * of maps that reuse one set of precomputed quantities, Sec. II.D.2, Sec. IV).
  *   plans     host array of B distinct plans that share N, L, interp and

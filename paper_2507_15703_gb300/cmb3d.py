@@ -71,6 +71,7 @@ PROTOTYPES = {
     "cmb3d_cl_matrix": (_i32, [_dp, _i32, _dp, _i32, C.c_double, _dp]),
     "cmb3d_realize_sample": (_i32, [_vp, _u64, _vp, _vp]),
     "cmb3d_realize_sample_to_host": (_i32, [_vp, _u64, _vp, _vp]),
+    "cmb3d_realize_samples_to_host": (_i32, [_vp, C.POINTER(_u64), _i32, C.POINTER(_vp), _vp]),
     "cmb3d_realize_sample_batch": (_i32, [C.POINTER(_vp), C.POINTER(_u64), C.POINTER(_vp), _i32, _vp]),
     "cmb3d_batch_debug": (None, [_u32, _i32, _i32]),
     "cmb3d_draw_spectrum": (_i32, [_vp, _u64, _vp, _vp]),
@@ -291,6 +292,21 @@ def cmb3d_realize_sample_to_host(plan: int, seed: int, out_host: np.ndarray, str
         raise ValueError("out_host must be a contiguous float32 array")
     _check(lib.cmb3d_realize_sample_to_host(plan, int(seed) & 0xFFFFFFFFFFFFFFFF, out_host.ctypes.data,
                                             _stream_ptr(stream)), "cmb3d_realize_sample_to_host")
+
+
+def cmb3d_realize_samples_to_host(plan: int, seeds, outs_host, stream=None) -> None:
+    """Maps of seeds[i] into the host arrays outs_host[i] (contiguous float32;
+    pinned memory lets each download overlap the next map's kernels)."""
+    lib = load()
+    n = len(seeds)
+    if len(outs_host) != n:
+        raise ValueError("seeds and outs_host must have equal lengths")
+    for o in outs_host:
+        if o.dtype != np.float32 or not o.flags.c_contiguous:
+            raise ValueError("every output must be a contiguous float32 array")
+    hs = (_u64 * max(n, 1))(*[int(s) & 0xFFFFFFFFFFFFFFFF for s in seeds])
+    ho = (_vp * max(n, 1))(*[o.ctypes.data for o in outs_host])
+    _check(lib.cmb3d_realize_samples_to_host(plan, hs, n, ho, _stream_ptr(stream)), "cmb3d_realize_samples_to_host")
 
 
 def cmb3d_realize_sample_batch(plans, seeds, outs_dev, stream=None) -> None:

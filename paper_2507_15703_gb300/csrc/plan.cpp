@@ -104,6 +104,12 @@ struct cmb3d_plan_s {
   float4* tab = nullptr;          // pixel table in gather order
   int32_t* perm = nullptr;        // gather order -> caller order (NULL = identity)
   float* outbuf = nullptr;        // staging for cmb3d_realize_sample_to_host
+  // cmb3d_realize_samples_to_host: a second staging buffer and a copy stream,
+  // so the download of map i overlaps the kernels of map i + 1; ev_mapped[k]:
+  // staging k holds a finished map, ev_copied[k]: staging k has been read.
+  float* outbuf2 = nullptr;
+  cudaStream_t cstream = nullptr;
+  cudaEvent_t ev_mapped[2] = {nullptr, nullptr}, ev_copied[2] = {nullptr, nullptr};
   unsigned* d_err = nullptr;      // set by a kernel whose bounded wait gave up
   int64_t dev_bytes = 0;
   bool has_spec = false;
@@ -179,11 +185,15 @@ void free_plan(cmb3d_plan_s* p) {
   DeviceGuard g(p->device);
   if (p->dstream) cudaStreamSynchronize(p->dstream);
   if (p->pstream) cudaStreamSynchronize(p->pstream);
-  for (cudaEvent_t ev : {p->ev_drawn[0], p->ev_drawn[1], p->ev_free[0], p->ev_free[1], p->ev_call})
+  if (p->cstream) cudaStreamSynchronize(p->cstream);
+  for (cudaEvent_t ev : {p->ev_drawn[0], p->ev_drawn[1], p->ev_free[0], p->ev_free[1], p->ev_call, p->ev_mapped[0],
+                         p->ev_mapped[1], p->ev_copied[0], p->ev_copied[1]})
     if (ev) cudaEventDestroy(ev);
   if (p->dstream) cudaStreamDestroy(p->dstream);
   if (p->pstream) cudaStreamDestroy(p->pstream);
+  if (p->cstream) cudaStreamDestroy(p->cstream);
   cudaFree(p->buf2);
+  cudaFree(p->outbuf2);
   p->batch.release();
   cudaFree(p->buf);
   cudaFree(p->amp);
@@ -1049,6 +1059,54 @@ int cmb3d_realize_sample_to_host(cmb3d_plan_t p, uint64_t seed, float* out_host,
     if (e != cudaSuccess) return fail_cuda(e, "map download");
   }
   cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail_cuda(e, "stream synchronize");
+  return check_device_error(p);
+}
+
+int cmb3d_realize_samples_to_host(cmb3d_plan_t p, const uint64_t* seeds, int count, float* const* outs_host,
+                                  void* stream) {
+  int st = check_ready(p);
+  if (st != CMB3D_OK) return st;
+  if (count < 0 || (count > 0 && (!seeds || !outs_host))) return fail(CMB3D_EINVAL, "seeds or outs_host is NULL");
+  for (int i = 0; i < count && p->npix > 0; ++i)
+    if (!outs_host[i]) return fail(CMB3D_EINVAL, "an output pointer is NULL");
+  DeviceGuard g(p->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaSuccess;
+  if (!p->cstream && p->npix > 0) {                   // first use: second staging buffer, copy stream, events
+    if ((st = dev_alloc(p, &p->outbuf2, static_cast<size_t>(p->npix), "second output staging")) != CMB3D_OK) return st;
+    e = cudaStreamCreateWithFlags(&p->cstream, cudaStreamNonBlocking);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+      e = cudaEventCreateWithFlags(&p->ev_mapped[k], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_copied[k], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) return fail_cuda(e, "copy stream setup");
+  }
+  const size_t bytes = static_cast<size_t>(p->npix) * sizeof(float);
+  for (int i = 0; i < count; ++i) {
+    const int k = i & 1;
+    float* staging = k ? p->outbuf2 : p->outbuf;
+    if (p->npix > 0 && (e = cudaStreamWaitEvent(s, p->ev_copied[k], 0)) != cudaSuccess)
+      return fail_cuda(e, "staging order");                                  // map i - 2 has been read
+    if (p->pipe) {
+      if ((st = run_map_pipelined(p, seeds[i], staging, s)) != CMB3D_OK) return st;
+    } else {
+      if ((st = run_field(p, seeds[i], s, true)) != CMB3D_OK) return st;
+      if ((st = run_gather(p, staging, s)) != CMB3D_OK) return st;
+    }
+    if (p->npix == 0) continue;
+    e = cudaEventRecord(p->ev_mapped[k], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->cstream, p->ev_mapped[k], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(outs_host[i], staging, bytes, cudaMemcpyDeviceToHost, p->cstream);
+    if (e == cudaSuccess) e = cudaEventRecord(p->ev_copied[k], p->cstream);
+    if (e != cudaSuccess) return fail_cuda(e, "map download");
+  }
+  if (p->cstream) {
+    e = cudaStreamWaitEvent(s, p->ev_copied[0], 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->ev_copied[1], 0);
+    if (e != cudaSuccess) return fail_cuda(e, "staging order");
+  }
+  e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return fail_cuda(e, "stream synchronize");
   return check_device_error(p);
 }

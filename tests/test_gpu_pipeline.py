@@ -117,3 +117,60 @@ def test_batch_of_pipelined_plans():
     finally:
         for p in plans + refs:
             p.close()
+
+
+@pytest.mark.parametrize("flags", [0, cmb3d.CMB3D_FLAG_PIPELINE, cmb3d.CMB3D_FLAG_STAGE_TIMING])
+def test_many_maps_to_host_equal_single_maps(flags):
+    """cmb3d_realize_samples_to_host: two staging buffers and a copy stream;
+    every map equals the single-call map bit for bit, in pinned and pageable
+    host memory, and a host buffer named twice holds its last map."""
+    N, L = 256, 2.2
+    kn, pk = smooth_pk(N, L)
+    pix = cap_pixels(128, 0.3)
+    seeds = [21, 22, 23, 24, 25]
+    with cmb3d.Plan(N, L, 1.0, pix, 3, flags) as plan, cmb3d.Plan(N, L, 1.0, pix, 3) as plain:
+        plan.set_pk(kn, pk)
+        plain.set_pk(kn, pk)
+        refs = [plain.realize_sample(sd).cpu().numpy() for sd in seeds]
+        pinned = [torch.empty(len(pix), dtype=torch.float32).pin_memory().numpy() for _ in seeds]
+        cmb3d.cmb3d_realize_samples_to_host(plan.handle, seeds, pinned)
+        for o, r in zip(pinned, refs):
+            np.testing.assert_array_equal(o, r)
+        pageable = [np.empty(len(pix), np.float32) for _ in range(2)]
+        cmb3d.cmb3d_realize_samples_to_host(plan.handle, seeds[:2], pageable)
+        np.testing.assert_array_equal(pageable[1], refs[1])
+        shared = np.empty(len(pix), np.float32)
+        cmb3d.cmb3d_realize_samples_to_host(plan.handle, seeds[:3], [shared] * 3)
+        np.testing.assert_array_equal(shared, refs[2])
+        cmb3d.cmb3d_realize_samples_to_host(plan.handle, [], [])
+        np.testing.assert_array_equal(plan.realize_sample(seeds[0]).cpu().numpy(), refs[0])   # still a plain plan
+        if flags & cmb3d.CMB3D_FLAG_STAGE_TIMING:
+            _, counts = cmb3d.cmb3d_stage_times(plan.handle)
+            assert list(counts) == [11] * 4 + [0]
+
+
+def test_many_maps_to_host_of_a_2d_plan():
+    from synth import cap_layers
+    N, M, dp = 128, 32, 0.0075
+    z0, h = cap_layers(20.0, dp)
+    kn, pk = smooth_pk(N, N * dp)
+    pix = cap_pixels(128, 0.03)
+    with cmb3d.Plan2D(N, M, h, N * dp, 1.0, z0, pix, 3, cmb3d.CMB3D_FLAG_PIPELINE) as plan:
+        plan.set_pk(kn, pk)
+        outs = [np.empty(len(pix), np.float32) for _ in range(3)]
+        cmb3d.cmb3d_realize_samples_to_host(plan.handle, [4, 5, 6], outs)
+        for sd, o in zip((4, 5, 6), outs):
+            np.testing.assert_array_equal(o, plan.realize_sample(sd).cpu().numpy())
+
+
+def test_many_maps_to_host_rejects_null_outputs():
+    N, L = 128, 2.2
+    kn, pk = smooth_pk(N, L)
+    with cmb3d.Plan(N, L, 1.0, cap_pixels(64, 0.2), 1) as plan:
+        plan.set_pk(kn, pk)
+        lib = cmb3d.load()
+        import ctypes as C
+        seeds = (C.c_uint64 * 2)(1, 2)
+        outs = (C.c_void_p * 2)(None, None)
+        assert lib.cmb3d_realize_samples_to_host(plan.handle, seeds, 2, outs, None) == cmb3d.CMB3D_EINVAL
+        assert lib.cmb3d_realize_samples_to_host(plan.handle, None, 2, outs, None) == cmb3d.CMB3D_EINVAL
