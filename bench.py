@@ -227,6 +227,8 @@ def run_cuda(args, rank, world, local):
         flags |= cmb3d.CMB3D_FLAG_NO_PRUNE
     if args.pipeline:
         flags |= cmb3d.CMB3D_FLAG_PIPELINE
+    if args.fused_xg:
+        flags |= cmb3d.CMB3D_FLAG_FUSED_XG
     if args.schedule:
         flags &= ~cmb3d.CMB3D_FLAG_AUTOTUNE
     if w.method == "2d":
@@ -356,7 +358,7 @@ def run_cuda(args, rank, world, local):
               "schedule": {"draw": schedule[0], "y": schedule[1], "x": schedule[2], "fused_yx": schedule[3],
                            "restriction": "three-pass" if args.three_pass else "fused" if args.fused else "autotuned",
                            "y_pass": "split-FP16 DFT-GEMM (tcgen05)" if args.fp16_gemm else "FP32 butterflies",
-                           "pipelined": bool(args.pipeline)},
+                           "pipelined": bool(args.pipeline), "fused_x_gather": bool(args.fused_xg)},
               "pruned_transform": {"z_planes": n_planes, "rows": n_rows, "of_planes": w.N, "of_rows": w.N ** 2,
                                    "note": "y pass on the z-planes, x pass on the (z, y) rows the "
                                            "interpolation stencils read; maps equal the whole-box maps bit for bit"},
@@ -742,6 +744,8 @@ def main():
     ap.add_argument("--three-pass", action="store_true", help="only separate y and x passes")
     ap.add_argument("--fused", action="store_true", help="only the fused y+x pass")
     ap.add_argument("--no-prune", action="store_true", help="transform the whole box for every map")
+    ap.add_argument("--fused-xg", action="store_true",
+                    help="sky maps with the x pass fused into the gather (CMB3D_FLAG_FUSED_XG)")
     ap.add_argument("--pipeline", action="store_true",
                     help="time the pipelined plan (two boxes, each map's draw overlapping the previous map's "
                          "passes and gather); by default it is timed after the main run and reported in config")

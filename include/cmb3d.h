@@ -82,13 +82,25 @@ enum {
                                          and stores only the (z, y) rows, and the x pass
                                          only the rows, that the pixels' interpolation
                                          stencils read; the maps are identical          */
-  CMB3D_FLAG_PIPELINE = 1u << 8       /* a second box (4 N^3 more bytes) and two
+  CMB3D_FLAG_PIPELINE = 1u << 8,      /* a second box (4 N^3 more bytes) and two
                                          internal streams: the draw of a sky map
                                          overlaps the passes and gather of the previous
                                          map of the plan.  Stream semantics are kept:
                                          the map's kernels run after the caller's stream
                                          at the call, and the caller's stream waits for
                                          the map.  Maps are identical                   */
+  CMB3D_FLAG_FUSED_XG = 1u << 9       /* sky maps run the x pass and the gather as one
+                                         kernel: pixels are grouped by 8 x 8 tiles of
+                                         (z, y) base cells, each tile's block forms the
+                                         real rows its stencils read in shared memory
+                                         (only the needed x columns) and interpolates
+                                         from there; the real field is never written.
+                                         32 <= N <= 2048 (no effect below); 20 more
+                                         bytes per pixel.  Maps equal those of the
+                                         separate passes with the x shape of the same
+                                         radix (x variant 1 at N = 1024; 0 else) bit
+                                         for bit.  Batches keep the separate
+                                         passes; cmb3d_realize_field is unchanged      */
 };
 
 /* Spectrum kinds for cmb3d_set_spectrum. */

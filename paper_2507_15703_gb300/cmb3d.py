@@ -36,6 +36,7 @@ CMB3D_FLAG_AUTOTUNE = 1 << 5
 CMB3D_FLAG_FP16_GEMM = 1 << 6
 CMB3D_FLAG_NO_PRUNE = 1 << 7
 CMB3D_FLAG_PIPELINE = 1 << 8
+CMB3D_FLAG_FUSED_XG = 1 << 9
 
 CMB3D_SPEC_PK = 0
 CMB3D_SPEC_CL = 1

@@ -136,15 +136,14 @@ __device__ __forceinline__ void yfft_tile(float2* __restrict__ plane, int x0, fl
 // the partner G[N/2 - k] comes from lane (NB - j) mod NB by a shuffle (entry
 // R-1-r there, or R-r for lane 0), otherwise through shared memory.
 // FIRST_SYNC: shared memory may still be read by an earlier step of the block.
-// The block's rows are rows[0 .. ROWS-1] (consecutive), or with `list` the rows
-// rows + list[rl] * N/2 for rl < ROWS.
-template <int N, int R, int ROWS, bool FIRST_SYNC = true>
-__device__ __forceinline__ void xc2r_rows(float2* __restrict__ rows, float2* sm, const float2* __restrict__ tw,
-                                          const int32_t* __restrict__ list = nullptr) {
+// `g` is the calling thread's row (N/2 packed entries, read through L2) and
+// store(n, y) receives entry n of the transformed row, y = (f(2n), f(2n+1)).
+template <int N, int R, int ROWS, bool FIRST_SYNC, class Store>
+__device__ __forceinline__ void xc2r_row_transform(const float2* g, float2* sm,
+                                                   const float2* __restrict__ tw, Store store) {
   constexpr int N2 = N / 2, NB = N2 / R;
   constexpr int P = N2 + (N2 >> 4);            // row pitch: one pad slot per 16 entries
   const int j = threadIdx.x % NB, rl = threadIdx.x / NB;
-  float2* g = rows + static_cast<size_t>(list ? __ldg(list + rl) : rl) * N2;
   auto sidx = [&](int n) { return rl * P + n + (n >> 4); };
   float2 v[R];
 #pragma unroll
@@ -167,7 +166,7 @@ __device__ __forceinline__ void xc2r_rows(float2* __restrict__ rows, float2* sm,
         v[r] = cadd(cadd(a, c), cmul_i(cmul(__ldg(tw + k), csub(a, c))));
       }
     }
-    stockham<N2, R, N, FIRST_SYNC>(v, sm, tw, j, sidx, [&](int n, float2 x) { g[n] = x; }, BlockSync{});
+    stockham<N2, R, N, FIRST_SYNC>(v, sm, tw, j, sidx, store, BlockSync{});
   } else {
 #pragma unroll
     for (int r = 0; r < R; ++r) sm[sidx(j + r * NB)] = v[r];
@@ -183,8 +182,19 @@ __device__ __forceinline__ void xc2r_rows(float2* __restrict__ rows, float2* sm,
         v[r] = cadd(cadd(a, c), cmul_i(cmul(__ldg(tw + k), csub(a, c))));
       }
     }
-    stockham<N2, R, N, true>(v, sm, tw, j, sidx, [&](int n, float2 x) { g[n] = x; }, BlockSync{});
+    stockham<N2, R, N, true>(v, sm, tw, j, sidx, store, BlockSync{});
   }
+}
+
+// The block's rows are rows[0 .. ROWS-1] (consecutive), or with `list` the rows
+// rows + list[rl] * N/2 for rl < ROWS; each is transformed in place.
+template <int N, int R, int ROWS, bool FIRST_SYNC = true>
+__device__ __forceinline__ void xc2r_rows(float2* __restrict__ rows, float2* sm, const float2* __restrict__ tw,
+                                          const int32_t* __restrict__ list = nullptr) {
+  constexpr int N2 = N / 2, NB = N2 / R;
+  const int rl = threadIdx.x / NB;
+  float2* g = rows + static_cast<size_t>(list ? __ldg(list + rl) : rl) * N2;
+  xc2r_row_transform<N, R, ROWS, FIRST_SYNC>(g, sm, tw, [&](int n, float2 x) { g[n] = x; });
 }
 
 }  // namespace cmb3d

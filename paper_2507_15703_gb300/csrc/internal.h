@@ -60,6 +60,30 @@ cudaError_t launch_xc2r(int N, int v, float2* buf, const float2* tw, cudaStream_
 // Interpolate the field float[z][y][x] at npix pixels.  tab[i] = (tx, ty, tz,
 // packed base cell) in gather order; out[perm[i]] receives pixel i (perm may
 // be NULL for the identity).
+// The x pass fused with the gather.  Pixels are grouped at plan time by the
+// kXgTile x kXgTile tile of (z, y) base cells they fall in; an entry is one
+// tile (or, where a tile's stencils reach more than kXgCols distinct x, a
+// part of it split by x).  Its block transforms the (z, y) rows the entry's
+// stencils read into a shared patch [slot][column] holding only the entry's
+// needed x columns, then interpolates its pixels from the patch with the
+// arithmetic of interpolate() (gather_tiles.cuh).  Row slot = lz S + ly for
+// local offsets lz, ly in [0, S), S = kXgTile + K - 1 (K taps per axis), at
+// global z = (z0 + lz + OFF) mod N (likewise y); padded slots are -1 and read
+// the scratch row.  The maps equal the separate x pass and gather bit for bit.
+constexpr int kXgTile = 8;
+constexpr int kXgCols = 64;
+struct XgEntry {
+  int32_t pix_begin, pix_end;    // pixels [pix_begin, pix_end) of the fused table
+  int32_t row_begin, nrows;      // rows [row_begin, row_begin + nrows) of the slot and row lists
+  int32_t col_begin, ncols;      // needed x columns, increasing
+  int32_t z0, y0;                // tile origin in base cells
+};
+int xgather_rows_per_block(int N);                    // rows per batch; row lists are padded to it
+bool xgather_supported(int N);
+cudaError_t launch_xgather(int N, int interp, const float2* buf, const float2* tw, const XgEntry* entries,
+                           int nentries, const int32_t* row_slot, const int32_t* row_glob, const int16_t* cols,
+                           const float4* tab, const int32_t* perm, float* out, cudaStream_t s);
+
 cudaError_t launch_gather(int N, int interp, const float* field, const float4* tab,
                           const int32_t* perm, float* out, int64_t npix, cudaStream_t s);
 

@@ -145,6 +145,17 @@ struct cmb3d_plan_s {
   // the pruned lists.
   int method = 3;
   int M = 0, h = 0;
+  // CMB3D_FLAG_FUSED_XG: sky maps run the x pass and the gather as one kernel
+  // (xgather.cu) on these entries, with the pixel table and permutation in
+  // entry order.
+  bool xg = false;
+  int xg_nentries = 0;
+  cmb3d::XgEntry* d_xg_entries = nullptr;
+  int32_t* d_xg_slot = nullptr;
+  int32_t* d_xg_row = nullptr;
+  int16_t* d_xg_cols = nullptr;
+  float4* d_xg_tab = nullptr;
+  int32_t* d_xg_perm = nullptr;
   double z0 = 0.0;
   float* sqt = nullptr;
   int32_t* d_planes_all = nullptr;
@@ -208,6 +219,12 @@ void free_plan(cmb3d_plan_s* p) {
   cudaFree(p->sqt);
   cudaFree(p->d_planes_all);
   cudaFree(p->d_rows_all);
+  cudaFree(p->d_xg_entries);
+  cudaFree(p->d_xg_slot);
+  cudaFree(p->d_xg_row);
+  cudaFree(p->d_xg_cols);
+  cudaFree(p->d_xg_tab);
+  cudaFree(p->d_xg_perm);
   for (auto& r : p->recs) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -413,6 +430,7 @@ int run_draw(cmb3d_plan_s* p, uint64_t seed, cudaStream_t s, float2* box) {
 // listed rows, in the separate-pass shapes of the schedule.
 int run_passes(cmb3d_plan_s* p, cudaStream_t s, bool prune, float2* box) {
   const Schedule& sc = p->sched;
+  const bool no_x = prune && p->xg;                   // the gather kernel runs the x pass
   cudaError_t e;
   if (p->method == 2) {                               // the h layers: y and x passes on lists
     const bool pr = prune && p->prune;
@@ -422,6 +440,7 @@ int run_passes(cmb3d_plan_s* p, cudaStream_t s, bool prune, float2* box) {
                                 static_cast<int>(pr ? p->nplanes : p->h), pr ? p->d_rowmask : nullptr);
     });
     if (e != cudaSuccess) return fail_cuda(e, "yfft launch");
+    if (no_x) return CMB3D_OK;
     e = timed(p, CMB3D_STAGE_XC2R, s, [&] {
       return cmb3d::launch_xc2r(p->N, xv, box, p->tw, s, pr ? p->d_rows : p->d_rows_all,
                                 pr ? p->nrows_pad : p->nrows_all_pad);
@@ -436,9 +455,15 @@ int run_passes(cmb3d_plan_s* p, cudaStream_t s, bool prune, float2* box) {
       return cmb3d::launch_yfft(p->N, yv, box, p->tw, s, p->d_planes, static_cast<int>(p->nplanes), p->d_rowmask);
     });
     if (e != cudaSuccess) return fail_cuda(e, "yfft launch");
+    if (no_x) return CMB3D_OK;
     e = timed(p, CMB3D_STAGE_XC2R, s,
               [&] { return cmb3d::launch_xc2r(p->N, xv, box, p->tw, s, p->d_rows, p->nrows_pad); });
     if (e != cudaSuccess) return fail_cuda(e, "xc2r launch");
+    return CMB3D_OK;
+  }
+  if (no_x) {                                         // whole-box y pass only
+    e = timed(p, CMB3D_STAGE_YFFT, s, [&] { return launch_y(p, sc.y >= 0 ? sc.y : 0, s, box); });
+    if (e != cudaSuccess) return fail_cuda(e, "yfft launch");
     return CMB3D_OK;
   }
   if (sc.fused >= 0) {
@@ -462,10 +487,15 @@ int run_field(cmb3d_plan_s* p, uint64_t seed, cudaStream_t s, bool prune) {
   return run_passes(p, s, prune, p->buf);
 }
 
+// Sampling of a sky map from `box`: the gather of the real field, or with the
+// fused form (p->xg) the x pass and the gather of the y-transformed box.
 int run_gather(cmb3d_plan_s* p, float* out, cudaStream_t s, const float2* box = nullptr) {
-  const float* field = reinterpret_cast<const float*>(box ? box : p->buf);
+  const float2* b = box ? box : p->buf;
   cudaError_t e = timed(p, CMB3D_STAGE_GATHER, s, [&] {
-    return cmb3d::launch_gather(p->N, p->interp, field, p->tab, p->perm, out, p->npix, s);
+    if (p->xg)
+      return cmb3d::launch_xgather(p->N, p->interp, b, p->tw, p->d_xg_entries, p->xg_nentries, p->d_xg_slot,
+                                   p->d_xg_row, p->d_xg_cols, p->d_xg_tab, p->d_xg_perm, out, s);
+    return cmb3d::launch_gather(p->N, p->interp, reinterpret_cast<const float*>(b), p->tab, p->perm, out, p->npix, s);
   });
   if (e != cudaSuccess) return fail_cuda(e, "gather launch");
   return CMB3D_OK;
@@ -529,6 +559,123 @@ const char* cmb3d_error_detail(void) { return g_detail.c_str(); }
 
 // Plan of the 3-D method (method 3) or of the 2-D Fourier method (method 2,
 // with M, h, z0); the two share the pixel table, pruning and the passes.
+namespace {
+
+// Entries of the fused x pass + gather (internal.h): the pixels grouped by
+// their tile of kXgTile x kXgTile (z, y) base cells, tiles in (z, y) order so
+// that neighbouring entries share halo rows in L2; a tile whose stencils
+// reach more than kXgCols distinct x is split into runs of increasing bx.
+struct XgHost {
+  std::vector<cmb3d::XgEntry> entries;
+  std::vector<int32_t> slot, row;
+  std::vector<int16_t> cols;
+  std::vector<float4> tab;
+  std::vector<int32_t> perm;
+};
+
+void build_xgather(int N, int nz, int interp, const std::vector<float4>& tab, const std::vector<int32_t>& perm,
+                   XgHost* xg) {
+  const int K = interp == CMB3D_TRICUBIC ? 4 : 2, OFF = interp == CMB3D_TRICUBIC ? -1 : 0;
+  const int T = cmb3d::kXgTile, SL = T + K - 1, ROWS = cmb3d::xgather_rows_per_block(N);
+  const int ntz = (nz + T - 1) / T, nty = N / T;
+  const size_t npix = tab.size();
+  std::vector<int32_t> bx(npix), by(npix), bz(npix);
+  std::vector<int64_t> start(static_cast<size_t>(ntz) * nty + 1, 0);
+  for (size_t i = 0; i < npix; ++i) {
+    uint32_t w, z;
+    std::memcpy(&w, &tab[i].w, sizeof(w));
+    std::memcpy(&z, &tab[i].z, sizeof(z));
+    bx[i] = static_cast<int32_t>(w & 2047u);
+    by[i] = static_cast<int32_t>((w >> 11) & 2047u);
+    bz[i] = static_cast<int32_t>((w >> 22) | ((z >> 31) << 10));
+    ++start[static_cast<size_t>(bz[i] / T) * nty + by[i] / T + 1];
+  }
+  for (size_t t = 1; t < start.size(); ++t) start[t] += start[t - 1];
+  std::vector<int32_t> order(npix);
+  {
+    std::vector<int64_t> fill(start.begin(), start.end() - 1);
+    for (size_t i = 0; i < npix; ++i)
+      order[static_cast<size_t>(fill[static_cast<size_t>(bz[i] / T) * nty + by[i] / T]++)] = static_cast<int32_t>(i);
+  }
+  std::vector<int> stamp(static_cast<size_t>(N), -1);
+  int group_id = 0;
+  auto emit = [&](const int32_t* g, size_t n, int tz, int ty) {
+    cmb3d::XgEntry e{};
+    e.z0 = tz * T;
+    e.y0 = ty * T;
+    e.pix_begin = static_cast<int32_t>(xg->tab.size());
+    e.col_begin = static_cast<int32_t>(xg->cols.size());
+    e.row_begin = static_cast<int32_t>(xg->slot.size());
+    std::vector<char> col(static_cast<size_t>(N), 0), used(static_cast<size_t>(SL) * SL, 0);
+    for (size_t k = 0; k < n; ++k) {
+      const size_t i = static_cast<size_t>(g[k]);
+      xg->tab.push_back(tab[i]);
+      xg->perm.push_back(perm.empty() ? static_cast<int32_t>(i) : perm[i]);
+      for (int a = 0; a < K; ++a) col[static_cast<size_t>((bx[i] + a + OFF + N) & (N - 1))] = 1;
+      const int lz = bz[i] - e.z0, ly = by[i] - e.y0;
+      for (int c = 0; c < K; ++c)
+        for (int b = 0; b < K; ++b) used[static_cast<size_t>((lz + c) * SL + ly + b)] = 1;
+    }
+    for (int x = 0; x < N; ++x)
+      if (col[static_cast<size_t>(x)]) xg->cols.push_back(static_cast<int16_t>(x));
+    for (int sl = 0; sl < SL * SL; ++sl) {
+      if (!used[static_cast<size_t>(sl)]) continue;
+      const int gz = ((e.z0 + sl / SL + OFF) % N + N) % N, gy = ((e.y0 + sl % SL + OFF) % N + N) % N;
+      xg->slot.push_back(sl);
+      xg->row.push_back(gz * N + gy);
+    }
+    while ((xg->slot.size() - static_cast<size_t>(e.row_begin)) % static_cast<size_t>(ROWS)) {
+      xg->slot.push_back(-1);                         // padding: the scratch row past the box
+      xg->row.push_back(nz * N);
+    }
+    e.pix_end = static_cast<int32_t>(xg->tab.size());
+    e.ncols = static_cast<int32_t>(xg->cols.size()) - e.col_begin;
+    e.nrows = static_cast<int32_t>(xg->slot.size()) - e.row_begin;
+    xg->entries.push_back(e);
+  };
+  for (int tz = 0; tz < ntz; ++tz)
+    for (int ty = 0; ty < nty; ++ty) {
+      const size_t t = static_cast<size_t>(tz) * nty + ty;
+      const int64_t b0 = start[t], b1 = start[t + 1];
+      if (b0 == b1) continue;
+      int ncols = 0;
+      ++group_id;
+      for (int64_t k = b0; k < b1; ++k)
+        for (int a = 0; a < K; ++a) {
+          int& st = stamp[static_cast<size_t>((bx[static_cast<size_t>(order[static_cast<size_t>(k)])] + a + OFF + N) &
+                                              (N - 1))];
+          if (st != group_id) st = group_id, ++ncols;
+        }
+      if (ncols <= cmb3d::kXgCols) {
+        emit(order.data() + b0, static_cast<size_t>(b1 - b0), tz, ty);
+        continue;
+      }
+      std::stable_sort(order.begin() + b0, order.begin() + b1,
+                       [&](int32_t u, int32_t v) { return bx[static_cast<size_t>(u)] < bx[static_cast<size_t>(v)]; });
+      int64_t g0 = b0;
+      ncols = 0;
+      ++group_id;
+      for (int64_t k = b0; k < b1; ++k) {
+        const int x0 = bx[static_cast<size_t>(order[static_cast<size_t>(k)])];
+        int add = 0;
+        for (int a = 0; a < K; ++a) add += stamp[static_cast<size_t>((x0 + a + OFF + N) & (N - 1))] != group_id;
+        if (ncols + add > cmb3d::kXgCols) {           // close the run before this pixel
+          emit(order.data() + g0, static_cast<size_t>(k - g0), tz, ty);
+          g0 = k;
+          ncols = 0;
+          ++group_id;
+        }
+        for (int a = 0; a < K; ++a) {
+          int& st = stamp[static_cast<size_t>((x0 + a + OFF + N) & (N - 1))];
+          if (st != group_id) st = group_id, ++ncols;
+        }
+      }
+      emit(order.data() + g0, static_cast<size_t>(b1 - g0), tz, ty);
+    }
+}
+
+}  // namespace
+
 static int create_plan(cmb3d_plan_t* out, int method, int N, int M, int h, double L, double r, double z0,
                        const double* pix_xyz, int64_t npix, int interp, uint32_t flags) {
   if (!out) return fail(CMB3D_EINVAL, "out is NULL");
@@ -551,7 +698,7 @@ static int create_plan(cmb3d_plan_t* out, int method, int N, int M, int h, doubl
   if (interp != CMB3D_TRILINEAR && interp != CMB3D_TRICUBIC) return fail(CMB3D_EINVAL, "interp must be 1 or 3");
   if (flags & ~uint32_t(CMB3D_FLAG_NO_SORT | CMB3D_FLAG_ALLOW_WRAP | CMB3D_FLAG_STAGE_TIMING | CMB3D_FLAG_THREE_PASS |
                         CMB3D_FLAG_FUSED_YX | CMB3D_FLAG_AUTOTUNE | CMB3D_FLAG_FP16_GEMM |
-                        CMB3D_FLAG_NO_PRUNE | CMB3D_FLAG_PIPELINE))
+                        CMB3D_FLAG_NO_PRUNE | CMB3D_FLAG_PIPELINE | CMB3D_FLAG_FUSED_XG))
     return fail(CMB3D_EINVAL, "unknown flag bits");
   if ((flags & CMB3D_FLAG_FP16_GEMM) && (flags & CMB3D_FLAG_FUSED_YX))
     return fail(CMB3D_EINVAL, "CMB3D_FLAG_FP16_GEMM uses separate y and x passes");
@@ -753,6 +900,38 @@ static int create_plan(cmb3d_plan_t* out, int method, int N, int M, int h, doubl
     p->nrows_pad = static_cast<int64_t>(rows.size());
     p->nrows = 0;
     for (int32_t rr : rows) p->nrows += rr < nz * N ? 1 : 0;
+  }
+  if (e == cudaSuccess && (flags & CMB3D_FLAG_FUSED_XG) && npix > 0 && cmb3d::xgather_supported(N)) {
+    XgHost xg;
+    try {
+      build_xgather(N, nz, interp, tab, perm, &xg);
+    } catch (const std::bad_alloc&) {
+      free_plan(p);
+      return fail(CMB3D_ENOMEM, "host allocation of the fused gather's entries");
+    }
+    if ((st = dev_alloc(p, &p->d_xg_entries, xg.entries.size(), "fused gather entries")) != CMB3D_OK ||
+        (st = dev_alloc(p, &p->d_xg_slot, xg.slot.size(), "fused gather slots")) != CMB3D_OK ||
+        (st = dev_alloc(p, &p->d_xg_row, xg.row.size(), "fused gather rows")) != CMB3D_OK ||
+        (st = dev_alloc(p, &p->d_xg_cols, xg.cols.size(), "fused gather columns")) != CMB3D_OK ||
+        (st = dev_alloc(p, &p->d_xg_tab, xg.tab.size(), "fused gather pixel table")) != CMB3D_OK ||
+        (st = dev_alloc(p, &p->d_xg_perm, xg.perm.size(), "fused gather permutation")) != CMB3D_OK) {
+      free_plan(p);
+      return st;
+    }
+    e = cudaMemcpy(p->d_xg_entries, xg.entries.data(), xg.entries.size() * sizeof(cmb3d::XgEntry),
+                   cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(p->d_xg_slot, xg.slot.data(), xg.slot.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(p->d_xg_row, xg.row.data(), xg.row.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(p->d_xg_cols, xg.cols.data(), xg.cols.size() * sizeof(int16_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(p->d_xg_tab, xg.tab.data(), xg.tab.size() * sizeof(float4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(p->d_xg_perm, xg.perm.data(), xg.perm.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    p->xg_nentries = static_cast<int>(xg.entries.size());
+    p->xg = e == cudaSuccess;
   }
   if (e == cudaSuccess && (flags & CMB3D_FLAG_PIPELINE)) {
     if ((st = dev_alloc(p, &p->buf2, nbuf, "second box")) != CMB3D_OK) {

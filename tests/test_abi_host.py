@@ -58,7 +58,7 @@ def test_plan_rejects_unsupported_sizes(lib, N):
     assert e.value.status == cmb3d.CMB3D_EUNSUPPORTED
 
 
-@pytest.mark.parametrize("kw", [dict(L=1.5), dict(L=-1.0), dict(r=0.0), dict(interp=2), dict(flags=1 << 9),
+@pytest.mark.parametrize("kw", [dict(L=1.5), dict(L=-1.0), dict(r=0.0), dict(interp=2), dict(flags=1 << 10),
                                 dict(L=float("nan"))])
 def test_plan_rejects_bad_arguments(lib, kw):
     args = dict(N=64, L=2.2, r=1.0, interp=1, flags=0)
@@ -153,7 +153,7 @@ def test_gamma_sqrt_table_matches_oracle(lib, N, M, h):
     (dict(N=8), "CMB3D_EUNSUPPORTED"), (dict(h=33), "CMB3D_EUNSUPPORTED"), (dict(N=16, h=20), "CMB3D_EUNSUPPORTED"),
     (dict(M=0), "CMB3D_EINVAL"), (dict(z0=float("nan")), "CMB3D_EINVAL"), (dict(L=0.0), "CMB3D_EINVAL"),
     (dict(flags=1 << 4), "CMB3D_EUNSUPPORTED"), (dict(flags=1 << 6), "CMB3D_EUNSUPPORTED"),
-    (dict(flags=1 << 9), "CMB3D_EINVAL")])
+    (dict(flags=1 << 10), "CMB3D_EINVAL")])
 def test_plan_2d_rejects_bad_arguments(lib, kw, status):
     args = dict(N=64, M=32, h=8, L=2.2, r=1.0, z0=0.5, flags=0)
     args.update(kw)
