@@ -35,6 +35,28 @@ __global__ void __launch_bounds__(T*(N / R)) k_draw_zfft(float2* __restrict__ bu
     draw_zfft_tile<N, R, T>(buf, amp, tw, key, blockIdx.x * T, blockIdx.y, sm);
 }
 
+// The same kernel compiled for 4 resident 256-thread blocks per SM, used for
+// the 4-column radix-8 tile (64 registers a thread; left to itself the
+// compiler takes 78 and fits 3 blocks, 2 % slower at N = 512).
+template <int N, int R, int T>
+__global__ void __launch_bounds__(256, 4) k_draw_zfft_b4(float2* __restrict__ buf, const float* __restrict__ amp,
+                                                         const float2* __restrict__ tw, uint2 key,
+                                                         const uint2* __restrict__ keyp) {
+  extern __shared__ float2 sm[];
+  if (keyp)
+    draw_zfft_tile<N, R, T>(buf, amp, tw, *keyp, blockIdx.x * T, blockIdx.y, sm);
+  else
+    draw_zfft_tile<N, R, T>(buf, amp, tw, key, blockIdx.x * T, blockIdx.y, sm);
+}
+
+template <int N, int R, int T>
+constexpr auto draw_kernel() {
+  if constexpr (R == 8 && T == 4 && T * (N / R) == 256)   // the 4-column radix-8 tile of 256 threads
+    return k_draw_zfft_b4<N, R, T>;
+  else
+    return k_draw_zfft<N, R, T>;
+}
+
 // y pass over z-planes blockIdx.y, or with `planes` over planes[blockIdx.y];
 // with `rowmask` (N bits per plane) only the marked rows are stored.
 template <int N, int R, int T>
@@ -253,7 +275,7 @@ template <int N, int R, int T>
 cudaError_t run_draw_zfft(float2* buf, const float* amp, const float2* tw, uint2 key, const uint2* keyp,
                           cudaStream_t s) {
   const size_t smem = sizeof(float2) * col_tile_elems<N, R, T>();
-  auto kern = k_draw_zfft<N, R, T>;
+  auto kern = draw_kernel<N, R, T>();
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   kern<<<dim3(N / 2 / T, N), T * (N / R), smem, s>>>(buf, amp, tw, key, keyp);
@@ -354,7 +376,7 @@ inline uint2 key_of(uint64_t seed) {
 //                                 distributed-shared-memory form, cluster of N/32 blocks
 // ---------------------------------------------------------------------------
 
-int num_col_variants(int N) { return N >= 256 ? 3 : 1; }
+int num_col_variants(int N) { return N >= 2048 ? 3 : N >= 256 ? 4 : 1; }
 int num_row_variants(int N) { return N >= 256 ? 3 : 1; }
 int num_fused_variants(int N) { return N == 128 ? 1 : (N == 256 || N == 512) ? 3 : N == 1024 ? 2 : 0; }
 
@@ -374,12 +396,15 @@ bool fused_variant_available(int N, int v) {
     case 256 * 4: return RUN<256, 8, 16>(__VA_ARGS__);                                     \
     case 256 * 4 + 1: return RUN<256, 16, 16>(__VA_ARGS__);                                \
     case 256 * 4 + 2: return RUN<256, 8, 8>(__VA_ARGS__);                                  \
+    case 256 * 4 + 3: return RUN<256, 8, 4>(__VA_ARGS__);                                  \
     case 512 * 4: return RUN<512, 8, 16>(__VA_ARGS__);                                     \
     case 512 * 4 + 1: return RUN<512, 16, 16>(__VA_ARGS__);                                \
     case 512 * 4 + 2: return RUN<512, 8, 8>(__VA_ARGS__);                                  \
+    case 512 * 4 + 3: return RUN<512, 8, 4>(__VA_ARGS__);                                  \
     case 1024 * 4: return RUN<1024, 16, 16>(__VA_ARGS__);                                  \
     case 1024 * 4 + 1: return RUN<1024, 16, 8>(__VA_ARGS__);                               \
     case 1024 * 4 + 2: return RUN<1024, 8, 8>(__VA_ARGS__);                                \
+    case 1024 * 4 + 3: return RUN<1024, 8, 4>(__VA_ARGS__);                                \
     case 2048 * 4: return RUN<2048, 16, 8>(__VA_ARGS__);                                   \
     case 2048 * 4 + 1: return RUN<2048, 16, 4>(__VA_ARGS__);                               \
     case 2048 * 4 + 2: return RUN<2048, 8, 4>(__VA_ARGS__);                                \

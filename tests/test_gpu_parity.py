@@ -153,7 +153,8 @@ def test_every_kernel_variant_matches_oracle(N):
     kn, pk = smooth_pk(N, L)
     pix = fibonacci_sphere(20000, 6007)
     ref = orc.realize_sample(N, L, 1.0, pix, orc.p_box_of_q(N, L, kn, pk), 17, 3)
-    scheds = [(d, 0, 0, -1) for d in range(3)] + [(0, y, 0, -1) for y in range(3)] + \
+    ncol = 3 if N >= 2048 else 4                     # draw / y shapes (radix, columns per tile)
+    scheds = [(d, 0, 0, -1) for d in range(ncol)] + [(0, y, 0, -1) for y in range(ncol)] + \
              [(0, 0, x, -1) for x in range(3)] + [(0, -1, -1, f) for f in range(3)]
     with cmb3d.Plan(N, L, 1.0, pix, 3, cmb3d.CMB3D_FLAG_NO_PRUNE) as plan:
         plan.set_pk(kn, pk)
@@ -163,7 +164,7 @@ def test_every_kernel_variant_matches_oracle(N):
             got = plan.realize_sample(17).cpu().numpy()
             assert rel_err(got, ref) <= TOL, sc
         with pytest.raises(cmb3d.Cmb3dError):
-            cmb3d.cmb3d_plan_set_schedule(plan.handle, (3, 0, 0, -1))
+            cmb3d.cmb3d_plan_set_schedule(plan.handle, (ncol, 0, 0, -1))
 
 
 def test_autotune_picks_valid_schedule():
@@ -174,7 +175,7 @@ def test_autotune_picks_valid_schedule():
         plan.set_pk(kn, pk)
         got = plan.realize_sample(2).cpu().numpy()
         d, y, x, f = cmb3d.cmb3d_plan_schedule(plan.handle)
-        assert 0 <= d < 3 and ((f >= 0 and y == x == -1) or (f == -1 and 0 <= y < 3 and 0 <= x < 3))
+        assert 0 <= d < 4 and ((f >= 0 and y == x == -1) or (f == -1 and 0 <= y < 4 and 0 <= x < 3))
     ref = orc.realize_sample(N, L, 1.0, pix, orc.p_box_of_q(N, L, kn, pk), 2, 3)
     assert rel_err(got, ref) <= TOL
 
