@@ -181,19 +181,21 @@ def alu_peak_tinst(clk) -> tuple[float, str]:
 
 
 def algorithmic_bytes(N: int, npix: int, planes: int | None = None, rows: int | None = None,
-                      nz: int | None = None) -> dict:
+                      nz: int | None = None, draw_planes: int | None = None) -> dict:
     """Bytes each kernel must move per launch (the packed half spectrum and the
     real field are both 4 N^2 nz bytes for nz z-planes, N for the 3-D box and
-    h layers for the 2-D method; a row is 4 N bytes): the draw writes the box
-    once; yfft reads its z-planes and writes its rows; xc2r reads and writes
-    its rows; gather reads 16 B of table + 4 B of permutation per pixel and
-    writes 4 B per pixel (field reads are cache-dependent and not counted).
-    planes, rows: the pruned extent of the sky-map path (default: whole box)."""
+    h layers for the 2-D method; a row is 4 N bytes): the draw writes the
+    draw_planes z-planes it stores (default: all); yfft reads its z-planes and
+    writes its rows; xc2r reads and writes its rows; gather reads 16 B of table
+    + 4 B of permutation per pixel and writes 4 B per pixel (field reads are
+    cache-dependent and not counted).  planes, rows: the pruned extent of the
+    sky-map path (default: whole box)."""
     nz = N if nz is None else nz
     box, row = 4 * N * N * nz, 4 * N
     planes = nz if planes is None else planes
     rows = nz * N if rows is None else rows
-    return {"draw_zfft": box, "yfft": planes * N * row + rows * row, "xc2r": 2 * rows * row,
+    drawn = 4 * N * N * (nz if draw_planes is None else draw_planes)
+    return {"draw_zfft": drawn, "yfft": planes * N * row + rows * row, "xc2r": 2 * rows * row,
             "gather": 24 * npix, "yx_fused": 2 * box}
 
 
@@ -342,7 +344,9 @@ def run_cuda(args, rank, world, local):
 
     maps = world * args.steps
     value = job_throughput(world, args.steps, t_max)
-    ab = algorithmic_bytes(w.N, npix, n_planes, n_rows, nlayers)
+    # the 3-D draw stores only the z-planes the pruned y pass reads; the 2-D
+    # draw writes all its layers
+    ab = algorithmic_bytes(w.N, npix, n_planes, n_rows, nlayers, nlayers if w.method == "2d" else n_planes)
     names = cmb3d.STAGE_NAMES
     kernels = {}
     for i, name in enumerate(names):

@@ -89,11 +89,12 @@ __device__ __forceinline__ void draw_packed_pair(int xp, int my, int mz, const f
 
 // Draw + inverse FFT along z of the T adjacent columns x0 .. x0+T-1 of row
 // m_y (blockDim.x == T * N / R): one thread draws the mode pairs
-// (m_z, m_z + N/2) of its column for its first-stage inputs.
+// (m_z, m_z + N/2) of its column for its first-stage inputs.  With `zmask`
+// (N bits) only the output planes z whose bit is set are stored.
 template <int N, int R, int T>
 __device__ __forceinline__ void draw_zfft_tile(float2* __restrict__ buf, const float* __restrict__ amp,
                                                const float2* __restrict__ tw, uint2 key, int x0, int my,
-                                               float2* sm) {
+                                               float2* sm, const uint32_t* __restrict__ zmask = nullptr) {
   constexpr int N2 = N / 2, NB = N / R;
   const int c = threadIdx.x % T, j = threadIdx.x / T;
   const int xp = x0 + c;
@@ -103,7 +104,10 @@ __device__ __forceinline__ void draw_zfft_tile(float2* __restrict__ buf, const f
   float2* col = buf + static_cast<size_t>(my) * N2 + xp;   // (z, my, xp) at col[z N N2]
   stockham<N, R, N, false>(
       v, sm, tw, j, [&](int n) { return col_slot<R, T>(n, c); },
-      [&](int n, float2 x) { col[static_cast<size_t>(n) * N * N2] = x; }, BlockSync{});
+      [&](int n, float2 x) {
+        if (!zmask || ((__ldg(zmask + (n >> 5)) >> (n & 31)) & 1u)) col[static_cast<size_t>(n) * N * N2] = x;
+      },
+      BlockSync{});
 }
 
 // In-place inverse FFT along y of the T adjacent columns x0 .. x0+T-1 of one

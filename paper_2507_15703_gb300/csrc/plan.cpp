@@ -129,6 +129,7 @@ struct cmb3d_plan_s {
   int32_t* d_planes = nullptr;
   int32_t* d_rows = nullptr;
   uint32_t* d_rowmask = nullptr;   // N bits per z-plane
+  uint32_t* d_zmask = nullptr;     // N bits: the listed z-planes (the draw stores only these for maps)
   // CMB3D_FLAG_PIPELINE: a second box and two internal streams; the draw of a
   // map (dstream) overlaps the passes and gather of the previous map (pstream,
   // higher priority).  ev_free[k]: box k's last gather done; ev_call: the
@@ -216,6 +217,7 @@ void free_plan(cmb3d_plan_s* p) {
   cudaFree(p->d_planes);
   cudaFree(p->d_rows);
   cudaFree(p->d_rowmask);
+  cudaFree(p->d_zmask);
   cudaFree(p->sqt);
   cudaFree(p->d_planes_all);
   cudaFree(p->d_rows_all);
@@ -413,12 +415,14 @@ int ensure_tuned(cmb3d_plan_s* p, cudaStream_t s) {
   return autotune(p, s);
 }
 
-// Draw fused with the z pass into `box`.
-int run_draw(cmb3d_plan_s* p, uint64_t seed, cudaStream_t s, float2* box) {
+// Draw fused with the z pass into `box`.  With `prune` (sky maps of a plan
+// with a pruned transform) only the z-planes the y pass reads are stored.
+int run_draw(cmb3d_plan_s* p, uint64_t seed, cudaStream_t s, float2* box, bool prune) {
   const Schedule& sc = p->sched;
   cudaError_t e = timed(p, CMB3D_STAGE_DRAW_ZFFT, s, [&] {
     if (p->method == 2) return cmb3d::launch_draw2d(p->N, p->h, box, p->sqt, seed, s);
-    return cmb3d::launch_draw_zfft(p->N, sc.draw, box, p->amp, p->tw, seed, s);
+    return cmb3d::launch_draw_zfft(p->N, sc.draw, box, p->amp, p->tw, seed, s, nullptr,
+                                   prune && p->prune ? p->d_zmask : nullptr);
   });
   if (e != cudaSuccess) return fail_cuda(e, "draw_zfft launch");
   return CMB3D_OK;
@@ -483,7 +487,7 @@ int run_field(cmb3d_plan_s* p, uint64_t seed, cudaStream_t s, bool prune) {
   int st = ensure_tuned(p, s);
   if (st != CMB3D_OK) return st;
   if (cudaError_t e = join_pipeline(p, s); e != cudaSuccess) return fail_cuda(e, "pipeline join");
-  if ((st = run_draw(p, seed, s, p->buf)) != CMB3D_OK) return st;
+  if ((st = run_draw(p, seed, s, p->buf, prune)) != CMB3D_OK) return st;
   return run_passes(p, s, prune, p->buf);
 }
 
@@ -517,7 +521,7 @@ int run_map_pipelined(cmb3d_plan_s* p, uint64_t seed, float* out, cudaStream_t s
   float2* box = k ? p->buf2 : p->buf;
   cudaError_t e = cudaStreamWaitEvent(p->dstream, p->ev_free[k], 0);
   if (e != cudaSuccess) return fail_cuda(e, "pipeline wait");
-  if ((st = run_draw(p, seed, p->dstream, box)) != CMB3D_OK) return st;
+  if ((st = run_draw(p, seed, p->dstream, box, true)) != CMB3D_OK) return st;
   e = cudaEventRecord(p->ev_drawn[k], p->dstream);
   if (e == cudaSuccess) e = cudaEventRecord(p->ev_call, s);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(p->pstream, p->ev_call, 0);
@@ -873,7 +877,8 @@ static int create_plan(cmb3d_plan_t* out, int method, int N, int M, int h, doubl
       (!perm.empty() && (st = dev_alloc(p, &p->perm, perm.size(), "permutation")) != CMB3D_OK) ||
       (!rows.empty() && ((st = dev_alloc(p, &p->d_rows, rows.size(), "row list")) != CMB3D_OK ||
                          (st = dev_alloc(p, &p->d_planes, planes.size(), "plane list")) != CMB3D_OK ||
-                         (st = dev_alloc(p, &p->d_rowmask, rowmask.size(), "row mask")) != CMB3D_OK))) {
+                         (st = dev_alloc(p, &p->d_rowmask, rowmask.size(), "row mask")) != CMB3D_OK ||
+                         (st = dev_alloc(p, &p->d_zmask, static_cast<size_t>((N + 31) / 32), "plane mask")) != CMB3D_OK))) {
     free_plan(p);
     return st;
   }
@@ -895,6 +900,11 @@ static int create_plan(cmb3d_plan_t* out, int method, int N, int M, int h, doubl
       e = cudaMemcpy(p->d_planes, planes.data(), planes.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
       e = cudaMemcpy(p->d_rowmask, rowmask.data(), rowmask.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+      std::vector<uint32_t> zmask(static_cast<size_t>((N + 31) / 32), 0u);
+      for (int32_t z : planes) zmask[static_cast<size_t>(z) >> 5] |= 1u << (z & 31);
+      e = cudaMemcpy(p->d_zmask, zmask.data(), zmask.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    }
     p->prune = true;
     p->nplanes = static_cast<int64_t>(planes.size());
     p->nrows_pad = static_cast<int64_t>(rows.size());
