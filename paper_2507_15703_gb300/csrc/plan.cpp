@@ -1262,41 +1262,53 @@ int cmb3d_realize_samples_to_host(cmb3d_plan_t p, const uint64_t* seeds, int cou
   DeviceGuard g(p->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaSuccess;
-  if (!p->cstream && p->npix > 0) {                   // first use: second staging buffer, copy stream, events
-    if ((st = dev_alloc(p, &p->outbuf2, static_cast<size_t>(p->npix), "second output staging")) != CMB3D_OK) return st;
+  if (p->npix > 0 && !p->outbuf2 &&               // first use: second staging buffer
+      (st = dev_alloc(p, &p->outbuf2, static_cast<size_t>(p->npix), "second output staging")) != CMB3D_OK)
+    return st;
+  if (p->npix > 0 && !p->cstream) {               // ... the copy stream and its events
     e = cudaStreamCreateWithFlags(&p->cstream, cudaStreamNonBlocking);
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
-      e = cudaEventCreateWithFlags(&p->ev_mapped[k], cudaEventDisableTiming);
-      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_copied[k], cudaEventDisableTiming);
+      if (!p->ev_mapped[k]) e = cudaEventCreateWithFlags(&p->ev_mapped[k], cudaEventDisableTiming);
+      if (e == cudaSuccess && !p->ev_copied[k]) e = cudaEventCreateWithFlags(&p->ev_copied[k], cudaEventDisableTiming);
     }
-    if (e != cudaSuccess) return fail_cuda(e, "copy stream setup");
+    if (e != cudaSuccess) {
+      if (p->cstream) cudaStreamDestroy(p->cstream);
+      p->cstream = nullptr;
+      return fail_cuda(e, "copy stream setup");
+    }
   }
+  // On an error every download already queued is waited for, so that no copy
+  // writes into the caller's host buffers after the call has returned.
+  auto abort_with = [&](int status) {
+    if (p->cstream) cudaStreamSynchronize(p->cstream);
+    return status;
+  };
   const size_t bytes = static_cast<size_t>(p->npix) * sizeof(float);
   for (int i = 0; i < count; ++i) {
     const int k = i & 1;
     float* staging = k ? p->outbuf2 : p->outbuf;
     if (p->npix > 0 && (e = cudaStreamWaitEvent(s, p->ev_copied[k], 0)) != cudaSuccess)
-      return fail_cuda(e, "staging order");                                  // map i - 2 has been read
+      return abort_with(fail_cuda(e, "staging order"));                     // map i - 2 has been read
     if (p->pipe) {
-      if ((st = run_map_pipelined(p, seeds[i], staging, s)) != CMB3D_OK) return st;
+      if ((st = run_map_pipelined(p, seeds[i], staging, s)) != CMB3D_OK) return abort_with(st);
     } else {
-      if ((st = run_field(p, seeds[i], s, true)) != CMB3D_OK) return st;
-      if ((st = run_gather(p, staging, s)) != CMB3D_OK) return st;
+      if ((st = run_field(p, seeds[i], s, true)) != CMB3D_OK) return abort_with(st);
+      if ((st = run_gather(p, staging, s)) != CMB3D_OK) return abort_with(st);
     }
     if (p->npix == 0) continue;
     e = cudaEventRecord(p->ev_mapped[k], s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(p->cstream, p->ev_mapped[k], 0);
     if (e == cudaSuccess) e = cudaMemcpyAsync(outs_host[i], staging, bytes, cudaMemcpyDeviceToHost, p->cstream);
     if (e == cudaSuccess) e = cudaEventRecord(p->ev_copied[k], p->cstream);
-    if (e != cudaSuccess) return fail_cuda(e, "map download");
+    if (e != cudaSuccess) return abort_with(fail_cuda(e, "map download"));
   }
   if (p->cstream) {
     e = cudaStreamWaitEvent(s, p->ev_copied[0], 0);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->ev_copied[1], 0);
-    if (e != cudaSuccess) return fail_cuda(e, "staging order");
+    if (e != cudaSuccess) return abort_with(fail_cuda(e, "staging order"));
   }
   e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return fail_cuda(e, "stream synchronize");
+  if (e != cudaSuccess) return abort_with(fail_cuda(e, "stream synchronize"));
   return check_device_error(p);
 }
 
