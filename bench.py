@@ -538,7 +538,7 @@ def run_cuda_batch(args, rank, world, local, w):
     value = job_throughput(world, args.steps * w.batch, t_max)
     batch_bytes = 24 * sum(npix)
     for zp, rw in extents:
-        ab = algorithmic_bytes(w.N, 0, zp, rw)
+        ab = algorithmic_bytes(w.N, 0, zp, rw, None, zp if pruned else None)   # pruned draws store zp planes
         batch_bytes += ab["draw_zfft"] + ab["yfft"] + ab["xc2r"]
     kernels = {"batch": kernel_entry(args.steps, ms, ms, batch_bytes)}
     kernels["batch"]["note"] = "one step = the whole batch (persistent kernel or graph), CUDA events"

@@ -1425,7 +1425,9 @@ int batch_streams(const cmb3d_plan_t* plans, const uint64_t* seeds, float* const
       for (int b = 0; b < B && el == cudaSuccess; ++b) {
         cmb3d_plan_s* p = plans[b];
         const Schedule& sc = p->sched;
-        el = cmb3d::launch_draw_zfft(N, sc.draw, p->buf, p->amp, p->tw, 0, bc.cap, bc.d_keys + b);
+        // with the pruned passes below, only the listed z-planes are stored
+        el = cmb3d::launch_draw_zfft(N, sc.draw, p->buf, p->amp, p->tw, 0, bc.cap, bc.d_keys + b,
+                                     p->prune ? p->d_zmask : nullptr);
         if (el == cudaSuccess) el = cudaEventRecord(ev[static_cast<size_t>(b)], bc.cap);
         if (el == cudaSuccess) el = cudaStreamWaitEvent(bc.cap2, ev[static_cast<size_t>(b)], 0);
         if (el == cudaSuccess) {
