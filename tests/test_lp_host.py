@@ -132,3 +132,20 @@ def test_bad_spectra_and_capacity(lib):
                              100.0, 4, kn.ctypes.data_as(dp), pk.ctypes.data_as(dp), C.byref(nk), C.byref(obj),
                              C.byref(err))
     assert st == cmb3d.CMB3D_EINVAL                                          # 4 < nk + 1
+
+
+def test_degenerate_programs_have_their_closed_forms(lib):
+    """One unknown (kmax = dk): the least x with A_i0 x >= b_i, i.e.
+    max_i b_i / A_i0.  One separation (r_max < dr, only r = 0): the objective
+    sum_i (A x)_i is (A x)_0 >= b_0, so its minimum is b_0 exactly."""
+    ell, cl = cl_family(128, 1e3, 22.0, 100.0)
+    _, _, A, b = cmb3d.cmb3d_lp_system(ell, cl, 1.0, 0.3, 0.0, 0.01, 2.0, 2.0)
+    assert A.shape == (60, 1) and np.all(A[:, 0] > 0)
+    kn, pk, obj, _ = cmb3d.cmb3d_fit_pk_lp(ell, cl, 1.0, 0.3, 0.0, 0.01, 2.0, 2.0)
+    assert len(pk) == 2 and pk[1] == 0.0
+    assert pk[0] == pytest.approx(np.max(b / A[:, 0]), rel=1e-12)
+    _, _, A1, b1 = cmb3d.cmb3d_lp_system(ell, cl, 1.0, 0.3, 0.0, 1.0, 0.0, 50.0)
+    assert A1.shape[0] == 1
+    _, pk1, obj1, err1 = cmb3d.cmb3d_fit_pk_lp(ell, cl, 1.0, 0.3, 0.0, 1.0, 0.0, 50.0)
+    assert obj1 == pytest.approx(b1[0], rel=1e-12) and err1 <= 1e-12
+    assert A1[0] @ pk1[:-1] == pytest.approx(b1[0], rel=1e-12)
