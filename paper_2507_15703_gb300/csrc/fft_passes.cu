@@ -26,14 +26,14 @@ template <int N, int R, int T>
 __global__ void __launch_bounds__(T*(N / R)) k_draw_zfft(float2* __restrict__ buf, const float* __restrict__ amp,
                                                          const float2* __restrict__ tw, uint2 key,
                                                          const uint2* __restrict__ keyp,
-                                                         const uint32_t* __restrict__ zmask) {
+                                                         const uint32_t* __restrict__ zmask, int zlo, int zhi) {
   extern __shared__ float2 sm[];
   // two copies of the body: with the key a kernel parameter its Philox round
   // keys stay in uniform registers, computed once per thread block
   if (keyp)
-    draw_zfft_tile<N, R, T>(buf, amp, tw, *keyp, blockIdx.x * T, blockIdx.y, sm, zmask);
+    draw_zfft_tile<N, R, T>(buf, amp, tw, *keyp, blockIdx.x * T, blockIdx.y, sm, zmask, zlo, zhi);
   else
-    draw_zfft_tile<N, R, T>(buf, amp, tw, key, blockIdx.x * T, blockIdx.y, sm, zmask);
+    draw_zfft_tile<N, R, T>(buf, amp, tw, key, blockIdx.x * T, blockIdx.y, sm, zmask, zlo, zhi);
 }
 
 // The same kernel compiled for 4 resident 256-thread blocks per SM, used for
@@ -43,12 +43,12 @@ template <int N, int R, int T>
 __global__ void __launch_bounds__(256, 4) k_draw_zfft_b4(float2* __restrict__ buf, const float* __restrict__ amp,
                                                          const float2* __restrict__ tw, uint2 key,
                                                          const uint2* __restrict__ keyp,
-                                                         const uint32_t* __restrict__ zmask) {
+                                                         const uint32_t* __restrict__ zmask, int zlo, int zhi) {
   extern __shared__ float2 sm[];
   if (keyp)
-    draw_zfft_tile<N, R, T>(buf, amp, tw, *keyp, blockIdx.x * T, blockIdx.y, sm, zmask);
+    draw_zfft_tile<N, R, T>(buf, amp, tw, *keyp, blockIdx.x * T, blockIdx.y, sm, zmask, zlo, zhi);
   else
-    draw_zfft_tile<N, R, T>(buf, amp, tw, key, blockIdx.x * T, blockIdx.y, sm, zmask);
+    draw_zfft_tile<N, R, T>(buf, amp, tw, key, blockIdx.x * T, blockIdx.y, sm, zmask, zlo, zhi);
 }
 
 template <int N, int R, int T>
@@ -275,12 +275,12 @@ cudaError_t run_yx_dsmem(float2* buf, const float2* tw, cudaStream_t s) {
 
 template <int N, int R, int T>
 cudaError_t run_draw_zfft(float2* buf, const float* amp, const float2* tw, uint2 key, const uint2* keyp,
-                          cudaStream_t s, const uint32_t* zmask) {
+                          cudaStream_t s, const uint32_t* zmask, int zlo, int zhi) {
   const size_t smem = sizeof(float2) * col_tile_elems<N, R, T>();
   auto kern = draw_kernel<N, R, T>();
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
-  kern<<<dim3(N / 2 / T, N), T * (N / R), smem, s>>>(buf, amp, tw, key, keyp, zmask);
+  kern<<<dim3(N / 2 / T, N), T * (N / R), smem, s>>>(buf, amp, tw, key, keyp, zmask, zlo, zhi > 0 ? zhi : N);
   return cudaGetLastError();
 }
 
@@ -414,9 +414,9 @@ bool fused_variant_available(int N, int v) {
   }
 
 cudaError_t launch_draw_zfft(int N, int v, float2* buf, const float* amp, const float2* tw, uint64_t seed,
-                             cudaStream_t s, const uint2* key_dev, const uint32_t* zmask) {
+                             cudaStream_t s, const uint2* key_dev, const uint32_t* zmask, int zlo, int zhi) {
   const uint2 key = key_of(seed);
-  CMB3D_COL_SWITCH(run_draw_zfft, buf, amp, tw, key, key_dev, s, zmask)
+  CMB3D_COL_SWITCH(run_draw_zfft, buf, amp, tw, key, key_dev, s, zmask, zlo, zhi)
 }
 
 cudaError_t launch_yfft(int N, int v, float2* buf, const float2* tw, cudaStream_t s, const int32_t* planes,

@@ -89,12 +89,14 @@ __device__ __forceinline__ void draw_packed_pair(int xp, int my, int mz, const f
 
 // Draw + inverse FFT along z of the T adjacent columns x0 .. x0+T-1 of row
 // m_y (blockDim.x == T * N / R): one thread draws the mode pairs
-// (m_z, m_z + N/2) of its column for its first-stage inputs.  With `zmask`
-// (N bits) only the output planes z whose bit is set are stored.
+// (m_z, m_z + N/2) of its column for its first-stage inputs.  Only output
+// planes z in [zlo, zhi) are stored, and with `zmask` (N bits) only those
+// whose bit is also set.
 template <int N, int R, int T>
 __device__ __forceinline__ void draw_zfft_tile(float2* __restrict__ buf, const float* __restrict__ amp,
                                                const float2* __restrict__ tw, uint2 key, int x0, int my,
-                                               float2* sm, const uint32_t* __restrict__ zmask = nullptr) {
+                                               float2* sm, const uint32_t* __restrict__ zmask = nullptr,
+                                               int zlo = 0, int zhi = N) {
   constexpr int N2 = N / 2, NB = N / R;
   const int c = threadIdx.x % T, j = threadIdx.x / T;
   const int xp = x0 + c;
@@ -105,7 +107,8 @@ __device__ __forceinline__ void draw_zfft_tile(float2* __restrict__ buf, const f
   stockham<N, R, N, false>(
       v, sm, tw, j, [&](int n) { return col_slot<R, T>(n, c); },
       [&](int n, float2 x) {
-        if (!zmask || ((__ldg(zmask + (n >> 5)) >> (n & 31)) & 1u)) col[static_cast<size_t>(n) * N * N2] = x;
+        if (n >= zlo && n < zhi && (!zmask || ((__ldg(zmask + (n >> 5)) >> (n & 31)) & 1u)))
+          col[static_cast<size_t>(n) * N * N2] = x;
       },
       BlockSync{});
 }

@@ -19,10 +19,11 @@ int num_row_variants(int N);
 int num_fused_variants(int N);
 
 // key_dev != NULL: read the Philox key (seed lo, seed hi) from device memory.
-// zmask != NULL (N bits): store only the output z-planes whose bit is set.
+// Only output z-planes in [zlo, zhi) are stored (zhi = 0: N), and with zmask
+// != NULL (N bits) only those whose bit is also set.
 cudaError_t launch_draw_zfft(int N, int v, float2* buf, const float* amp, const float2* tw,
                              uint64_t seed, cudaStream_t s, const uint2* key_dev = nullptr,
-                             const uint32_t* zmask = nullptr);
+                             const uint32_t* zmask = nullptr, int zlo = 0, int zhi = 0);
 
 // 2-D Fourier method: the hybrid layers [z][m_y][m_x'] (h <= 32 layers) from
 // the per-q table of z-covariance square roots (h x h floats per q).

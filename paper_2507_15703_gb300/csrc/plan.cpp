@@ -130,6 +130,7 @@ struct cmb3d_plan_s {
   int32_t* d_rows = nullptr;
   uint32_t* d_rowmask = nullptr;   // N bits per z-plane
   uint32_t* d_zmask = nullptr;     // N bits: the listed z-planes (the draw stores only these for maps)
+  int zlo = 0, zhi = 0;            // listed z-planes as one range [zlo, zhi) when contiguous (then no mask)
   // CMB3D_FLAG_PIPELINE: a second box and two internal streams; the draw of a
   // map (dstream) overlaps the passes and gather of the previous map (pstream,
   // higher priority).  ev_free[k]: box k's last gather done; ev_call: the
@@ -421,8 +422,9 @@ int run_draw(cmb3d_plan_s* p, uint64_t seed, cudaStream_t s, float2* box, bool p
   const Schedule& sc = p->sched;
   cudaError_t e = timed(p, CMB3D_STAGE_DRAW_ZFFT, s, [&] {
     if (p->method == 2) return cmb3d::launch_draw2d(p->N, p->h, box, p->sqt, seed, s);
+    const bool pr = prune && p->prune;
     return cmb3d::launch_draw_zfft(p->N, sc.draw, box, p->amp, p->tw, seed, s, nullptr,
-                                   prune && p->prune ? p->d_zmask : nullptr);
+                                   pr && p->zhi == 0 ? p->d_zmask : nullptr, pr ? p->zlo : 0, pr ? p->zhi : 0);
   });
   if (e != cudaSuccess) return fail_cuda(e, "draw_zfft launch");
   return CMB3D_OK;
@@ -904,6 +906,10 @@ static int create_plan(cmb3d_plan_t* out, int method, int N, int M, int h, doubl
       std::vector<uint32_t> zmask(static_cast<size_t>((N + 31) / 32), 0u);
       for (int32_t z : planes) zmask[static_cast<size_t>(z) >> 5] |= 1u << (z & 31);
       e = cudaMemcpy(p->d_zmask, zmask.data(), zmask.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+      if (!planes.empty() && planes.back() - planes.front() + 1 == static_cast<int32_t>(planes.size())) {
+        p->zlo = planes.front();                      // contiguous: a range test, no mask reads
+        p->zhi = planes.back() + 1;
+      }
     }
     p->prune = true;
     p->nplanes = static_cast<int64_t>(planes.size());
@@ -1427,7 +1433,8 @@ int batch_streams(const cmb3d_plan_t* plans, const uint64_t* seeds, float* const
         const Schedule& sc = p->sched;
         // with the pruned passes below, only the listed z-planes are stored
         el = cmb3d::launch_draw_zfft(N, sc.draw, p->buf, p->amp, p->tw, 0, bc.cap, bc.d_keys + b,
-                                     p->prune ? p->d_zmask : nullptr);
+                                     p->prune && p->zhi == 0 ? p->d_zmask : nullptr, p->prune ? p->zlo : 0,
+                                     p->prune ? p->zhi : 0);
         if (el == cudaSuccess) el = cudaEventRecord(ev[static_cast<size_t>(b)], bc.cap);
         if (el == cudaSuccess) el = cudaStreamWaitEvent(bc.cap2, ev[static_cast<size_t>(b)], 0);
         if (el == cudaSuccess) {
