@@ -3,8 +3,10 @@ the 2-D Fourier method with --workload fourier2d_box512_cap20).
 
 One step = one complete map of the workload through the C ABI: Philox draw
 fused with the z-FFT, y-FFT, x complex-to-real FFT and the tricubic gather at
-the cap pixels.  Default workload: a 512^3 box (L = 2.2 r) sampled at the
-5,033,165 pixels of an f_sky = 0.4 polar cap of a 12*1024^2-point grid.
+the cap pixels.  Default workload: a 1024^3 box (L = 2.2 r) sampled at the
+20,132,659 pixels of an f_sky = 0.4 polar cap of a 12*2048^2-point grid; the
+512^3 box with the 5,033,165-pixel cap of a 12*1024^2-point grid is timed
+after it and reported in config as a secondary figure.
 
 The line printed by rank 0 carries maps/s (device-timed, inputs resident),
 the end-to-end figure through the host-buffer entry point, the roofline of
@@ -38,7 +40,8 @@ sys.path.insert(0, ROOT)
 
 from synth import WORKLOADS  # noqa: E402
 
-DEFAULT_WORKLOAD = "box512_cap0.4_tricubic"
+DEFAULT_WORKLOAD = "box1024_cap0.4_tricubic"
+SECONDARY_WORKLOAD = "box512_cap0.4_tricubic"
 METRIC = "partial-sky maps/sec and achieved HBM GB/s at N^3 box, Npix pixels, 1 GB300"
 L2_BYTES = 129 * 2 ** 20
 
@@ -80,7 +83,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "20"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, ValueError):
             self.proc = None
             return
@@ -180,6 +183,14 @@ def alu_peak_tinst(clk) -> tuple[float, str]:
     return sms * 128 * mhz * 1e6 / 1e12, f"derived: {sms} SMs x 4 schedulers x 32 lanes x {mhz:.0f} MHz"
 
 
+def b_alg_bytes(N: int, npix: int) -> int:
+    """The whole-map algorithmic minimum of the unpruned 3-D method: one write
+    and one read of the complex half spectrum between the axes (2 H, H = 8 N^2
+    (N/2 + 1) bytes), one write of the real field (4 N^3) and 20 B per pixel
+    (16 B table + 4 B output)."""
+    return 2 * 8 * N * N * (N // 2 + 1) + 4 * N ** 3 + 20 * npix
+
+
 def algorithmic_bytes(N: int, npix: int, planes: int | None = None, rows: int | None = None,
                       nz: int | None = None, draw_planes: int | None = None) -> dict:
     """Bytes each kernel must move per launch (the packed half spectrum and the
@@ -249,6 +260,8 @@ def run_cuda(args, rank, world, local):
         fit_err = plan.set_cl(ell, cl, w.nkbins)
         kn_fit = np.linspace(0.0, math.sqrt(3) * math.pi * w.N / w.L, w.nkbins)   # the fit's nodes
         plan_pk = (kn_fit, cmb3d.cmb3d_get_pk(plan.handle, kn_fit))
+        rel_fit = (cmb3d.cmb3d_cl_matrix(ell, kn_fit, w.r) @ plan_pk[1] - cl) / cl
+        fit_rms = float(np.sqrt(np.mean(rel_fit ** 2)))
     setup_s = time.time() - t0
     stream = torch.cuda.current_stream(dev)
     out = torch.empty(npix, dtype=torch.float32, device=dev)
@@ -338,6 +351,10 @@ def run_cuda(args, rank, world, local):
                              "passes and gather (timed after the main run, same maps and stream)"}
     plan.close()
 
+    secondary = None
+    if rank == 0 and args.workload == DEFAULT_WORKLOAD and not args.no_secondary:
+        secondary = secondary_figure(args, dev, stream, seed0)
+
     if rank != 0:
         finish_dist(dist)
         return
@@ -367,7 +384,11 @@ def run_cuda(args, rank, world, local):
                                    "note": "y pass on the z-planes, x pass on the (z, y) rows the "
                                            "interpolation stencils read; maps equal the whole-box maps bit for bit"},
               "l2": f"no flush: per-map working set {per_map_bytes / 2**30:.2f} GiB > 129 MiB L2",
-              "cl_fit_max_rel_err": fit_err, "plan_setup_s": round(setup_s, 2),
+              "cl_fit_max_rel_err": fit_err,
+              "cl_fit_rms_rel_err": None if learned is not None else round(fit_rms, 4),
+              "cl_fit_note": None if learned is not None else
+              "NNLS optimum of a P >= 0 on the nodes for this oscillating C_l family, not a solver failure",
+              "plan_setup_s": round(setup_s, 2),
               "method": ({"name": "2-D Fourier method (Sec. II.D.2)", "M": w.M, "h": nlayers,
                           "z0": round(z0, 6), "dp": w.dp, "theta_max_deg": w.theta_max_deg}
                          if w.method == "2d" else {"name": "3-D Fourier method (Sec. II.D.1)"}),
@@ -375,6 +396,20 @@ def run_cuda(args, rank, world, local):
               "e2e_one_call_per_map_maps_per_s": round(world * args.steps / e2e_sync_s, 3),
               "e2e_d2h_ms_per_map": round(d2h_ms, 4),
               "e2e_d2h_gbs": round(4 * npix / (d2h_ms / 1e3) / 1e9, 1)}
+    if w.method != "2d":
+        ba = b_alg_bytes(w.N, npix)
+        config["pipeline_bytes"] = {
+            "b_alg_unpruned_per_map": ba,
+            "b_alg_gbs": round(ba * value / world / 1e9, 1),
+            "b_alg_frac_of_measured_hbm": round(ba * value / world / 1e9 / measured_peaks()[0], 4),
+            "moved_pruned_per_map": per_map_bytes,
+            "moved_gbs": round(per_map_bytes * value / world / 1e9, 1),
+            "moved_frac_of_measured_hbm": round(per_map_bytes * value / world / 1e9 / measured_peaks()[0], 4),
+            "note": "b_alg: the unpruned method's algorithmic minimum (write + read of the half spectrum, "
+                    "field write, 20 B per pixel) per map at the measured map rate; moved: the bytes the "
+                    "pruned kernels actually have to move (per-kernel algorithmic bytes summed)"}
+    if secondary is not None:
+        config["secondary"] = secondary
     if learned is not None:
         config["cl_fit_max_rel_err"] = None
         config["spectrum"] = "P(k) of held-out spectrum 0 from the learned inversion"
@@ -388,6 +423,37 @@ def run_cuda(args, rank, world, local):
     emit(args, w, value, t_max, world, config, per_map_bytes, kernels, dom, maps / e2e_s, 4 * npix,
          int(stage_n.sum()), clk)
     finish_dist(dist)
+
+
+def secondary_figure(args, dev, stream, seed0, maps=50):
+    """The 512^3 single-map workload timed on the same GPU after the main run
+    (its own autotuned plan, CUDA events over `maps` maps): maps/s and the
+    per-kernel times."""
+    import torch
+    from paper_2507_15703_gb300 import cmb3d
+    w = WORKLOADS[SECONDARY_WORKLOAD]
+    pix = w.pixels()
+    ell, cl = w.cl()
+    plan = cmb3d.Plan(w.N, w.L, w.r, pix, w.interp, cmb3d.CMB3D_FLAG_STAGE_TIMING | cmb3d.CMB3D_FLAG_AUTOTUNE)
+    plan.set_cl(ell, cl, w.nkbins)
+    out = torch.empty(pix.shape[0], dtype=torch.float32, device=dev)
+    for i in range(max(args.warmup, 3)):
+        plan.realize_sample(seed0 + i, out, stream)
+    torch.cuda.synchronize(dev)
+    cmb3d.cmb3d_stage_times(plan.handle, reset=True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for i in range(maps):
+        plan.realize_sample(seed0 + 100 + i, out, stream)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = ev0.elapsed_time(ev1)
+    st_ms, st_n = cmb3d.cmb3d_stage_times(plan.handle, reset=True)
+    plan.close()
+    return {"workload": SECONDARY_WORKLOAD, "maps": maps, "maps_per_s": round(maps / (ms / 1e3), 1),
+            "ms_per_map": round(ms / maps, 5),
+            "kernel_ms": {name: round(float(st_ms[k] / st_n[k]), 5)
+                          for k, name in enumerate(cmb3d.STAGE_NAMES) if st_n[k]}}
 
 
 def train_learned_inversion(args, w, dev):
@@ -696,13 +762,16 @@ def oracle_map_sample(w, seed):
     return time.perf_counter() - t, vals.size
 
 
+ORACLE_THREADS = 1   # numpy's pocketfft and its elementwise array operations run on the calling thread
+
+
 def cpu_baseline(w, args):
     """The oracle, as it stands, timed on one full map of the same workload on
     the host cores (numpy FP64; one map is the bounded sample)."""
-    threads = os.cpu_count()
     secs, _ = oracle_map_sample(w, 0)
-    return {"value": round(1.0 / secs, 6), "unit": "maps/s", "cores": threads, "kind": "oracle",
-            "sample": f"one full map of {args.workload} by the numpy FP64 oracle ({secs:.1f} s)"}
+    return {"value": round(1.0 / secs, 6), "unit": "maps/s", "cores": ORACLE_THREADS, "kind": "oracle",
+            "sample": f"one full map of {args.workload} by the numpy FP64 oracle ({secs:.1f} s; "
+                      f"{os.cpu_count()} host cores present, numpy's FFT and array operations use one)"}
 
 
 def run_reference(args, rank, world):
@@ -729,7 +798,7 @@ def run_reference(args, rank, world):
             "steps": len(times), "warmup": warm, "ms_per_step": round(1e3 * total / len(times), 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": args.workload, "N": w.N, "npix": int(w.pixels().shape[0])},
-            "cpu_baseline": {"value": round(value, 6), "unit": "maps/s", "cores": os.cpu_count(), "kind": "oracle",
+            "cpu_baseline": {"value": round(value, 6), "unit": "maps/s", "cores": ORACLE_THREADS, "kind": "oracle",
                              "sample": f"{len(times)} full map(s) of {args.workload} by the numpy FP64 oracle "
                                        f"(bounded to about {args.ref_budget_s:.0f} s)"},
             "e2e": {"value": round(value, 6), "unit": "maps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -745,6 +814,7 @@ def main():
     ap.add_argument("--impl", default="cmb3d", choices=["cmb3d", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the secondary 512^3 figure")
     ap.add_argument("--three-pass", action="store_true", help="only separate y and x passes")
     ap.add_argument("--fused", action="store_true", help="only the fused y+x pass")
     ap.add_argument("--no-prune", action="store_true", help="transform the whole box for every map")

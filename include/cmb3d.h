@@ -424,6 +424,8 @@ int cmb3d_stage_times(cmb3d_plan_t plan, double* ms, int64_t* launches, int n, i
  *            CMB3D_EUNSUPPORTED (the box does not fit the static scratch).
  *   L, r     box side and sphere radius, finite, > 0, L > 2r (CMB3D_EINVAL).
  *   pix_dev  device pointer, npix x 3 doubles (unit vectors, row-major).
+ *            Not validated: a pixel whose grid coordinate is not finite (or
+ *            beyond 4e15 cells) reads no memory and receives NaN.
  *   npix     0 <= npix < 2^31.
  *   interp   CMB3D_TRILINEAR or CMB3D_TRICUBIC.
  *   amp_dev  device pointer, 3 (N/2)^2 + 1 floats: amp[q] = sqrt(P_box(q) / 2)
@@ -431,12 +433,18 @@ int cmb3d_stage_times(cmb3d_plan_t plan, double* ms, int64_t* launches, int n, i
  *            cmb3d_set_spectrum builds for a plan.
  *   out_dev  device pointer, npix floats, written in pixel order.
  * The box and twiddle tables live in one static __device__ array of about
- * 1 MiB that every GPU loading the library holds until the process exits.
- * The first call on a device looks up that array's address and uploads the
- * twiddle tables with a synchronous copy, so make it before any stream
- * capture.  Every call overwrites the whole box before use, but all calls
- * share the array: calls that overlap on the GPU (other streams or threads)
- * race and must be serialised by the caller.  Calls no allocating routine.
+ * 1 MiB.  The driver places it when it loads the library's module on a
+ * device; under lazy module loading (CUDA_MODULE_LOADING=LAZY, the runtime's
+ * default) that is the first call on that device, so a caller that must see
+ * no allocation later makes one warm-up call at start-up.  The array stays
+ * until the device's context is destroyed.  The first call in a device
+ * context looks up the array's address and uploads the twiddle tables with a
+ * synchronous copy, so make it before any stream capture; after
+ * cudaDeviceReset the next call repeats that set-up.  Every call overwrites
+ * the whole box before use, but all calls share the array: calls that overlap
+ * on the GPU (other streams or threads) race and must be serialised by the
+ * caller.  Calls no allocating routine of its own.  On a rejected call,
+ * cmb3d_error_detail() gives the reason.
  */
 #define CMB3D_NOALLOC_MAX_N 64
 int cmb3d_realize_sample_noalloc(int N, double L, double r, const double* pix_dev, int64_t npix, int interp,
@@ -515,6 +523,22 @@ int cmb3d_mlp_loss_grad(cmb3d_mlp_t mlp, const float* logcl_dev, int64_t n, doub
 int cmb3d_mlp_params(cmb3d_mlp_t mlp, float* get_host, const float* set_host, int64_t* count);
 
 void cmb3d_mlp_destroy(cmb3d_mlp_t mlp);
+
+/*
+ * Diagnostic: the network's matrix-product kernel on caller data, so that it
+ * can be compared element by element with exact sums.  Every product of the
+ * learned inversion runs through it (forward layers, the forward relation of
+ * paper Sec. II.A, and the transposed products of the backward pass).
+ *   out[m os0 + n os1] = f(alpha sum_k bf16(a[m as0 + k as1]) bf16(b[n bs0 + k bs1]) + bias[n])
+ * for m < M, n < N, with operands rounded to bfloat16 (nearest, ties to even),
+ * FP32 accumulation in tensor memory, f = GELU if gelu != 0 else identity,
+ * bias (device, N floats) may be NULL.  a, b, out: device FP32, any strides
+ * (so either operand may be transposed).  Synchronises on `stream`;
+ * CMB3D_ETIMEOUT if a bounded wait for MMA completion gave up.
+ */
+int cmb3d_mlp_gemm(int M, int N, int K, const float* a, int64_t as0, int64_t as1, const float* b, int64_t bs0,
+                   int64_t bs1, float alpha, const float* bias, int gelu, float* out, int64_t os0, int64_t os1,
+                   void* stream);
 
 /* Message of the most recent MLP error on the calling thread. */
 const char* cmb3d_mlp_error_detail(void);

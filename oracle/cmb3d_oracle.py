@@ -413,35 +413,59 @@ def gelu_grad(x):
     return 0.5 * (1.0 + erf(x / np.sqrt(2.0))) + x * np.exp(-0.5 * x * x) / np.sqrt(2.0 * np.pi)
 
 
-def mlp_loss_grad(params, n_in, width, depth, n_out, A, mu, sd, logc):
+def bf16_round(x) -> np.ndarray:
+    """Each value taken as binary32 and rounded to the nearest bfloat16 (8-bit
+    significand, ties to even), returned in float64: the operand precision of
+    the network's matrix products (BF16 operands, FP32 accumulation)."""
+    f = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+    b = f.view(np.uint32).astype(np.uint64)
+    b = (b + np.uint64(0x7FFF) + ((b >> np.uint64(16)) & np.uint64(1))) & np.uint64(0xFFFF0000)
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def mlp_loss_grad(params, n_in, width, depth, n_out, A, mu, sd, logc, operands=None):
     """Loss mean((log(A exp(y)) - log C)^2) of the network with the given flat
     parameters on spectra logc (n x n_in), and its gradient (flat), by the
-    chain rule written out layer by layer."""
+    chain rule written out layer by layer.
+
+    operands="bf16": both operands of every matrix product (the layers, the
+    forward relation and their transposes in the backward pass) are first
+    rounded to bfloat16 and the products summed exactly, the definition of the
+    mixed-precision network (BF16 operands, FP32 accumulation; the rounding is
+    passed through unchanged by the chain rule).  The forward relation is then
+    taken shifted by each row's largest y, log(A exp(y)) = ymax + log(A
+    exp(y - ymax)), so the rounded operand is exp(y - ymax) <= 1; without
+    rounding the shift changes nothing and is not made."""
+    rnd = bf16_round if operands == "bf16" else (lambda v: v)
+    if operands not in (None, "bf16"):
+        raise ValueError("operands must be None or 'bf16'")
     p = np.asarray(params, dtype=np.float64)
     dims, offs, total = mlp_shapes(n_in, width, depth, n_out)
     Ws = [p[o:o + d[0] * d[1]].reshape(d) for d, (o, _) in zip(dims, offs)]
     bs = [p[ob:ob + d[0]] for d, (_, ob) in zip(dims, offs)]
     logc = np.asarray(logc, dtype=np.float64)
+    A = np.asarray(A, np.float64)
     x = (logc - np.asarray(mu, np.float64)) / np.asarray(sd, np.float64)
     zs, acts = [], [x]
     for l in range(depth):
-        z = acts[-1] @ Ws[l].T + bs[l]
+        z = rnd(acts[-1]) @ rnd(Ws[l]).T + bs[l]
         zs.append(z)
         acts.append(gelu(z))
-    y = acts[-1] @ Ws[depth].T + bs[depth]
-    E = np.exp(y)
-    P = E @ np.asarray(A, np.float64).T
-    d = np.log(P) - logc
+    y = rnd(acts[-1]) @ rnd(Ws[depth]).T + bs[depth]
+    ymax = y.max(axis=1, keepdims=True) if operands == "bf16" else 0.0
+    E = np.exp(y - ymax)
+    P = rnd(E) @ rnd(A).T
+    d = np.log(P) + ymax - logc
     cnt = d.size
     loss = float(np.sum(d * d) / cnt)
     dP = 2.0 * d / cnt / P
-    dY = (dP @ np.asarray(A, np.float64)) * E
+    dY = (rnd(dP) @ rnd(A)) * E
     g = np.zeros(total)
     dcur = dY
     for l in range(depth, -1, -1):
         o, ob = offs[l]
-        g[o:o + dims[l][0] * dims[l][1]] = (dcur.T @ acts[l]).ravel()
+        g[o:o + dims[l][0] * dims[l][1]] = (rnd(dcur).T @ rnd(acts[l])).ravel()
         g[ob:ob + dims[l][0]] = dcur.sum(axis=0)
         if l > 0:
-            dcur = (dcur @ Ws[l]) * gelu_grad(zs[l - 1])
+            dcur = (rnd(dcur) @ rnd(Ws[l])) * gelu_grad(zs[l - 1])
     return loss, g

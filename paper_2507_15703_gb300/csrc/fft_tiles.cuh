@@ -87,27 +87,94 @@ __device__ __forceinline__ void draw_packed_pair(int xp, int my, int mz, const f
   hi = make_float2(a_hi * g1.x, a_hi * g1.y);
 }
 
-// Draw + inverse FFT along z of the T adjacent columns x0 .. x0+T-1 of row
-// m_y (blockDim.x == T * N / R): one thread draws the mode pairs
-// (m_z, m_z + N/2) of its column for its first-stage inputs.  Only output
-// planes z in [zlo, zhi) are stored, and with `zmask` (N bits) only those
-// whose bit is also set.
-template <int N, int R, int T>
+// Pitch (floats) of one column's amplitude row in the draw's exchange area:
+// at least N/2 + 1, and = 32/T mod 32, so that the T columns x 32/T rows of a
+// warp hit 32 distinct banks.
+template <int N, int T>
+__host__ __device__ constexpr int amp_pitch() {
+  return (N / 2 + 1 + 31 - ((32 / T) % 32)) / 32 * 32 + (32 / T) % 32;
+}
+// Shared floats of the draw tile beyond its FFT tile (the amplitude exchange).
+template <int N, int T>
+__host__ __device__ constexpr int draw_amp_floats() {
+  return T * amp_pitch<N, T>();
+}
+
+// Which columns a draw tile covers.
+enum DrawTileKind {
+  kDrawMixed = 0,     // T columns x0 .. x0+T-1 of row m_y; a lane on m_x' = 0 takes the Hermitian path
+  kDrawRegular = 1,   // the same, but a lane on m_x' = 0 draws nothing and stores nothing
+  kDrawHermitian = 2  // the packed Hermitian column m_x' = 0 of the T rows m_y = x0 .. x0+T-1
+};
+
+// Draw + inverse FFT along z of T columns (blockDim.x == T * N / R): one
+// thread draws the mode pairs (m_z, m_z + N/2) of its column for its
+// first-stage inputs.  Only output planes z in [zlo, zhi) are stored, and with
+// `zmask` (N bits) only those whose bit is also set.
+//
+// kDrawRegular: the amplitude of mode (m_x', m_y, m_z) depends on |f_z| only
+// through q = m_x'^2 + f_y^2 + f_z^2, and the thread drawing m_z < N/2 needs
+// |f_z| = m_z for the first mode of a pair and N/2 - m_z for the second, which
+// is the first mode's |f_z| of thread NB - j.  So each thread reads only its
+// first modes' amplitudes from the table (one L2 sector each), shares them
+// through shared memory (`sa`: draw_amp_floats<N, T>() floats past the FFT
+// tile) and takes the second modes' from there: half the table traffic.
+template <int N, int R, int T, int KIND = kDrawMixed>
 __device__ __forceinline__ void draw_zfft_tile(float2* __restrict__ buf, const float* __restrict__ amp,
                                                const float2* __restrict__ tw, uint2 key, int x0, int my,
                                                float2* sm, const uint32_t* __restrict__ zmask = nullptr,
                                                int zlo = 0, int zhi = N) {
-  constexpr int N2 = N / 2, NB = N / R;
+  constexpr int N2 = N / 2, NB = N / R, H = N / 2;
   const int c = threadIdx.x % T, j = threadIdx.x / T;
-  const int xp = x0 + c;
   float2 v[R];
+  float2* col;
+  bool store = true;
+  if constexpr (KIND == kDrawRegular) {
+    constexpr int P = amp_pitch<N, T>();
+    const int xp = x0 + c;
+    store = xp != 0;
+    float* sa = reinterpret_cast<float*>(sm + col_tile_elems<N, R, T>()) + c * P;
+    const int fy = my <= H ? my : my - N;
+    const int base = xp * xp + fy * fy;
+    float alo[R / 2];
 #pragma unroll
-  for (int r = 0; r < R / 2; ++r) draw_packed_pair<N>(xp, my, j + r * NB, amp, key, v[r], v[r + R / 2]);
-  float2* col = buf + static_cast<size_t>(my) * N2 + xp;   // (z, my, xp) at col[z N N2]
+    for (int r = 0; r < R / 2; ++r) alo[r] = __ldg(amp + base + (j + r * NB) * (j + r * NB));
+    const float anyq = j == 0 ? __ldg(amp + base + H * H) : 0.0f;
+#pragma unroll
+    for (int r = 0; r < R / 2; ++r) {
+      const uint4 w = philox4x32_10(make_uint4(xp, my, j + r * NB, 0u), key);
+      const float2 g0 = box_muller(w.x, w.y);
+      v[r] = make_float2(alo[r] * g0.x, alo[r] * g0.y);
+      v[r + R / 2] = box_muller(w.z, w.w);
+      sa[j + r * NB] = alo[r];
+    }
+    if (j == 0) sa[H] = anyq;
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < R / 2; ++r) {
+      const float a = sa[H - j - r * NB];
+      v[r + R / 2] = make_float2(a * v[r + R / 2].x, a * v[r + R / 2].y);
+    }
+    if (!store) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = make_float2(0.f, 0.f);
+    }
+    col = buf + static_cast<size_t>(my) * N2 + xp;            // (z, my, xp) at col[z N N2]
+  } else if constexpr (KIND == kDrawHermitian) {
+    const int row = x0 + c;
+#pragma unroll
+    for (int r = 0; r < R / 2; ++r) draw_packed_pair<N>(0, row, j + r * NB, amp, key, v[r], v[r + R / 2]);
+    col = buf + static_cast<size_t>(row) * N2;
+  } else {
+    const int xp = x0 + c;
+#pragma unroll
+    for (int r = 0; r < R / 2; ++r) draw_packed_pair<N>(xp, my, j + r * NB, amp, key, v[r], v[r + R / 2]);
+    col = buf + static_cast<size_t>(my) * N2 + xp;
+  }
   stockham<N, R, N, false>(
       v, sm, tw, j, [&](int n) { return col_slot<R, T>(n, c); },
       [&](int n, float2 x) {
-        if (n >= zlo && n < zhi && (!zmask || ((__ldg(zmask + (n >> 5)) >> (n & 31)) & 1u)))
+        if (store && n >= zlo && n < zhi && (!zmask || ((__ldg(zmask + (n >> 5)) >> (n & 31)) & 1u)))
           col[static_cast<size_t>(n) * N * N2] = x;
       },
       BlockSync{});

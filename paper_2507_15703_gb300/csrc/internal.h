@@ -7,6 +7,10 @@
 
 namespace cmb3d {
 
+// Set the message cmb3d_error_detail() returns on this host thread (entry
+// points outside plan.cpp use it to report why a call was rejected).
+void set_error_detail(const char* msg);
+
 // Packed half-spectrum buffer: float2 [N][N][N/2]; entry m_x' = 0 holds
 // T(0,.,.) + i T(N/2,.,.).  After the three passes it holds float [N][N][N].
 

@@ -530,4 +530,31 @@ int cmb3d_mlp_params(cmb3d_mlp_t h, float* get_host, const float* set_host, int6
 
 void cmb3d_mlp_destroy(cmb3d_mlp_t h) { free_mlp(h); }
 
+int cmb3d_mlp_gemm(int M, int N, int K, const float* a, int64_t as0, int64_t as1, const float* b, int64_t bs0,
+                   int64_t bs1, float alpha, const float* bias, int gelu, float* out, int64_t os0, int64_t os1,
+                   void* stream) {
+  if (M < 1 || N < 1 || K < 1 || !a || !b || !out) return mfail(CMB3D_EINVAL, "bad GEMM shape or NULL pointer");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned* err = nullptr;
+  if (cudaMalloc(&err, sizeof(unsigned)) != cudaSuccess) {
+    cudaGetLastError();
+    return mfail(CMB3D_ENOMEM, "error word");
+  }
+  cudaError_t e = cudaMemsetAsync(err, 0, sizeof(unsigned), s);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
+  if (e == cudaSuccess) {
+    dim3 grid((N + kTile - 1) / kTile, (M + kTile - 1) / kTile);
+    k_gemm<<<grid, 128, kGemmSmem, s>>>(M, N, K, Mat{a, as0, as1}, Mat{b, bs0, bs1}, alpha, bias, nullptr, out, os0,
+                                        os1, gelu ? 1 : 0, err);
+    e = cudaGetLastError();
+  }
+  unsigned v = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&v, err, sizeof(v), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(err);
+  if (e != cudaSuccess) return mfail(CMB3D_ECUDA, cudaGetErrorString(e));
+  if (v) return mfail(CMB3D_ETIMEOUT, "a bounded wait for MMA completion gave up");
+  return CMB3D_OK;
+}
+
 }  // extern "C"

@@ -8,12 +8,16 @@
 //
 // The box (4 N^3 bytes) and the twiddle tables live in one file-scope
 // __device__ array of fixed size, sized for N <= CMB3D_NOALLOC_MAX_N (64):
-// about 1 MiB that every GPU which loads the library keeps until the process
-// exits.  In host code the array's name only stands in for it; its device
-// address is obtained once per device with cudaGetSymbolAddress and passed to
-// the kernels.  All calls share the array: each call overwrites the whole box
-// before reading it, so no state carries over, but calls whose work overlaps
-// on the GPU (different streams, or different host threads) race on it.
+// about 1 MiB.  The driver places it when it loads this module on a device;
+// under lazy module loading (the CUDA runtime's default) that happens at the
+// first call on that device, and the array then stays until the context is
+// destroyed.  In host code the array's name only stands in for it; its device
+// address is obtained once per device context with cudaGetSymbolAddress and
+// passed to the kernels.  The set-up is redone when the device's context
+// changes (cudaDeviceReset), detected by the context's unique id.  All calls
+// share the array: each call overwrites the whole box before reading it, so no
+// state carries over, but calls whose work overlaps on the GPU (different
+// streams, or different host threads) race on it.
 #include <cmath>
 #include <mutex>
 
@@ -35,23 +39,57 @@ __device__ __align__(256) unsigned char g_noalloc_scratch[kBoxBytes + kTwBytes];
 
 struct DeviceState {
   bool ready = false;
+  unsigned long long ctx_id = 0;                      // unique id of the context set up
   unsigned char* base = nullptr;                      // device address of g_noalloc_scratch
 };
 constexpr int kMaxDevices = 64;
 DeviceState g_state[kMaxDevices];
 std::mutex g_mu;
-float2 g_host_tw[kTwEntries];                         // staging for the one-time upload
+float2 g_host_tw[kTwEntries];                         // staging for the set-up upload
 
 int tw_offset(int N) { return N == 8 ? 0 : N == 16 ? 8 : N == 32 ? 24 : 56; }
 
-// Once per device, with that device current: look up the array's device
-// address and upload the twiddle tables (a synchronous host-to-device copy).
+// Unique id of the calling thread's current context (CUDA driver entry points
+// cuCtxGetCurrent and cuCtxGetId, looked up through the runtime so the library
+// does not link libcuda).  0 if the driver does not provide them: the set-up
+// is then kept for the life of the process.
+unsigned long long current_context_id() {
+  using GetCurrent = int (*)(void**);
+  using GetId = int (*)(void*, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrent>(f);
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetId>(f);
+    cudaGetLastError();
+  });
+  void* ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+  return id;
+}
+
+// Once per device context, with that device current: look up the array's
+// device address and upload the twiddle tables (a synchronous host-to-device
+// copy).  cudaSetDevice on the current device makes its primary context
+// current first, so the context id is that of the context the kernels run in.
 int setup(int dev, unsigned char** base) {
   std::lock_guard<std::mutex> lock(g_mu);
   DeviceState& st = g_state[dev];
-  if (!st.ready) {
+  cudaError_t e = cudaSetDevice(dev);
+  if (e != cudaSuccess) return static_cast<int>(e);
+  const unsigned long long id = current_context_id();
+  if (!st.ready || id != st.ctx_id) {
+    st.ready = false;
     void* ptr = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
     if (e != cudaSuccess) return static_cast<int>(e);
     for (int s = 0, N = 8; s < kNumSizes; ++s, N *= 2)
       for (int m = 0; m < N; ++m) {
@@ -61,6 +99,7 @@ int setup(int dev, unsigned char** base) {
     e = cudaMemcpy(static_cast<unsigned char*>(ptr) + kBoxBytes, g_host_tw, sizeof(g_host_tw), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return static_cast<int>(e);
     st.base = static_cast<unsigned char*>(ptr);
+    st.ctx_id = id;
     st.ready = true;
   }
   *base = st.base;
@@ -103,9 +142,14 @@ __global__ void __launch_bounds__(256) k_gather_xyz(const float* __restrict__ fi
   const double half_l = 0.5 * L;
   uint32_t b[3];
   float t[3];
+  bool finite = true;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const double u = __ddiv_rn(__dadd_rn(__dmul_rn(r, pix[3 * static_cast<size_t>(i) + a]), half_l), dp);
+    double u = __ddiv_rn(__dadd_rn(__dmul_rn(r, pix[3 * static_cast<size_t>(i) + a]), half_l), dp);
+    if (!(fabs(u) < 4.0e15)) {                        // not finite, or beyond exact integer cells
+      finite = false;
+      u = 0.0;
+    }
     const double fl = floor(u);
     long long bi = static_cast<long long>(fl) % N;
     if (bi < 0) bi += N;
@@ -135,12 +179,14 @@ __global__ void __launch_bounds__(256) k_gather_xyz(const float* __restrict__ fi
     }
     acc = fmaf(wz[c], accz, acc);
   }
-  out[i] = acc;
+  out[i] = finite ? acc : __int_as_float(0x7FC00000);  // NaN marks a pixel that cannot be placed
 }
 
-// Status of a rejected call; the message documents the reason in the source
-// (the public error detail belongs to the plan API).
-int fail(int status, const char* /*reason*/) { return status; }
+// Status of a rejected call; the reason is what cmb3d_error_detail() returns.
+int fail(int status, const char* reason) {
+  cmb3d::set_error_detail(reason);
+  return status;
+}
 
 }  // namespace
 
@@ -165,6 +211,7 @@ extern "C" int cmb3d_realize_sample_noalloc(int N, double L, double r, const dou
     cudaGetLastError();
     return fail(CMB3D_ECUDA, "static scratch set-up failed (cudaGetSymbolAddress or twiddle upload)");
   }
+  cmb3d::set_error_detail("");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   float2* box = reinterpret_cast<float2*>(base);
   const float2* tw = reinterpret_cast<const float2*>(base + kBoxBytes) + tw_offset(N);

@@ -33,6 +33,12 @@ int fail_cuda(cudaError_t e, const char* where) {
   return CMB3D_ECUDA;
 }
 
+}  // namespace
+
+void cmb3d::set_error_detail(const char* msg) { g_detail = msg ? msg : ""; }
+
+namespace {
+
 struct TimingRec {
   int stage;
   cudaEvent_t a, b;
