@@ -519,6 +519,21 @@ int cmb3d_mlp_predict(cmb3d_mlp_t mlp, const float* logcl_dev, int64_t n, float*
 int cmb3d_mlp_loss_grad(cmb3d_mlp_t mlp, const float* logcl_dev, int64_t n, double* loss_host, float* grad_dev,
                         void* stream);
 
+/*
+ * Refine predicted spectra toward the non-negative least-squares optimum of
+ * the forward relation (paper Sec. II.A: C_l = sum_j A[l, j] P(k_j)): P >= 0
+ * minimising sum_l ((A P)_l / C_l - 1)^2, the objective of the NNLS inversion
+ * of cmb3d_set_spectrum(CMB3D_SPEC_CL), by `iters` steps of accelerated
+ * projected gradient (FISTA) started at exp(logpk), in the variable P / s with
+ * s_j the inverse norm of column j of diag(1/C) A, step 1/L from a
+ * `power_iters`-step power iteration (times 1.05).  Every product runs through
+ * the network's BF16-operand, FP32-accumulate GEMM kernel.
+ *   logcl_dev  device, n x n_in floats (log C_l);  logpk_dev  device, n x n_out (start, log P)
+ *   pk_dev     device, n x n_out floats (result P, not log).  Synchronous.
+ */
+int cmb3d_mlp_refine(cmb3d_mlp_t mlp, const float* logcl_dev, const float* logpk_dev, int64_t n, int iters,
+                     int power_iters, float* pk_dev, void* stream);
+
 /* Parameter count (*count), read (get_host) and / or write (set_host), host floats. */
 int cmb3d_mlp_params(cmb3d_mlp_t mlp, float* get_host, const float* set_host, int64_t* count);
 

@@ -91,6 +91,7 @@ PROTOTYPES = {
     "cmb3d_mlp_loss_grad": (_i32, [_vp, _vp, _i64, _dp, _vp, _vp]),
     "cmb3d_mlp_params": (_i32, [_vp, _vp, _vp, C.POINTER(_i64)]),
     "cmb3d_mlp_destroy": (None, [_vp]),
+    "cmb3d_mlp_refine": (_i32, [_vp, _vp, _vp, _i64, _i32, _i32, _vp, _vp]),
     "cmb3d_mlp_gemm": (_i32, [_i32, _i32, _i32, _vp, _i64, _i64, _vp, _i64, _i64, C.c_float, _vp, _i32, _vp, _i64,
                               _i64, _vp]),
     "cmb3d_mlp_error_detail": (C.c_char_p, []),
@@ -483,6 +484,15 @@ def cmb3d_mlp_destroy(mlp) -> None:
 
 def cmb3d_mlp_error_detail() -> str:
     return load().cmb3d_mlp_error_detail().decode()
+
+
+def cmb3d_mlp_refine(mlp, logcl_dev, logpk_dev, n: int, pk_dev, iters: int = 300, power_iters: int = 30,
+                     stream=None) -> None:
+    """P >= 0 refined from exp(logpk) toward the NNLS optimum of the forward
+    relation (FISTA, the network's GEMM kernel); result in pk_dev (not log)."""
+    lib = load()
+    _mcheck(lib.cmb3d_mlp_refine(mlp, _dev_ptr(logcl_dev), _dev_ptr(logpk_dev), int(n), int(iters), int(power_iters),
+                                 _dev_ptr(pk_dev), _stream_ptr(stream)), "cmb3d_mlp_refine")
 
 
 def cmb3d_mlp_gemm(M: int, N: int, K: int, a, a_strides, b, b_strides, out, out_strides, alpha: float = 1.0,

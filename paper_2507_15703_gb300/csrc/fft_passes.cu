@@ -51,13 +51,13 @@ __global__ void __launch_bounds__(T*(N / R)) k_draw_zfft(float2* __restrict__ bu
     draw_block<N, R, T>(buf, amp, tw, key, sm, zmask, zlo, zhi);
 }
 
-// The same kernel compiled for 4 resident 256-thread blocks per SM, used for
-// the 4-column radix-8 tile (64 registers a thread).
-template <int N, int R, int T>
-__global__ void __launch_bounds__(256, 4) k_draw_zfft_b4(float2* __restrict__ buf, const float* __restrict__ amp,
-                                                         const float2* __restrict__ tw, uint2 key,
-                                                         const uint2* __restrict__ keyp,
-                                                         const uint32_t* __restrict__ zmask, int zlo, int zhi) {
+// The same kernel compiled for MINB resident 256-thread blocks per SM: 4 for
+// radix 8 (64 registers a thread), 2 for radix 16 (128 registers).
+template <int N, int R, int T, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_draw_zfft_mb(float2* __restrict__ buf, const float* __restrict__ amp,
+                                                            const float2* __restrict__ tw, uint2 key,
+                                                            const uint2* __restrict__ keyp,
+                                                            const uint32_t* __restrict__ zmask, int zlo, int zhi) {
   extern __shared__ float2 sm[];
   if (keyp)
     draw_block<N, R, T>(buf, amp, tw, *keyp, sm, zmask, zlo, zhi);
@@ -67,8 +67,8 @@ __global__ void __launch_bounds__(256, 4) k_draw_zfft_b4(float2* __restrict__ bu
 
 template <int N, int R, int T>
 constexpr auto draw_kernel() {
-  if constexpr (R == 8 && T == 4 && T * (N / R) == 256)   // the 4-column radix-8 tile of 256 threads
-    return k_draw_zfft_b4<N, R, T>;
+  if constexpr (T * (N / R) == 256)                   // 256-thread tiles: several blocks per SM
+    return k_draw_zfft_mb<N, R, T, (R == 8 ? 4 : 2)>;
   else
     return k_draw_zfft<N, R, T>;
 }
@@ -393,6 +393,9 @@ inline uint2 key_of(uint64_t seed) {
 // ---------------------------------------------------------------------------
 
 int num_col_variants(int N) { return N >= 2048 ? 3 : N >= 256 ? 4 : 1; }
+int num_draw_variants(int N) {
+  return (N >= 1024 ? num_col_variants(N) + 2 : num_col_variants(N)) + (draw_tc_supported(N) ? 1 : 0);
+}
 int num_row_variants(int N) { return N >= 256 ? 3 : 1; }
 int num_fused_variants(int N) { return N == 128 ? 1 : (N == 256 || N == 512) ? 3 : N == 1024 ? 2 : 0; }
 
@@ -428,8 +431,16 @@ bool fused_variant_available(int N, int v) {
   }
 
 cudaError_t launch_draw_zfft(int N, int v, float2* buf, const float* amp, const float2* tw, uint64_t seed,
-                             cudaStream_t s, const uint2* key_dev, const uint32_t* zmask, int zlo, int zhi) {
+                             cudaStream_t s, const uint2* key_dev, const uint32_t* zmask, int zlo, int zhi,
+                             unsigned* err) {
+  if (draw_tc_supported(N) && v == num_draw_variants(N) - 1)
+    return launch_draw_tc(N, buf, amp, tw, seed, s, err, key_dev, zmask, zlo, zhi);
   const uint2 key = key_of(seed);
+  // draw-only shapes beyond the column-pass table: 256-thread tiles at N >= 1024
+  if (N == 1024 && v == 4) return run_draw_zfft<1024, 16, 4>(buf, amp, tw, key, key_dev, s, zmask, zlo, zhi);
+  if (N == 1024 && v == 5) return run_draw_zfft<1024, 8, 2>(buf, amp, tw, key, key_dev, s, zmask, zlo, zhi);
+  if (N == 2048 && v == 3) return run_draw_zfft<2048, 16, 2>(buf, amp, tw, key, key_dev, s, zmask, zlo, zhi);
+  if (N == 2048 && v == 4) return run_draw_zfft<2048, 8, 1>(buf, amp, tw, key, key_dev, s, zmask, zlo, zhi);
   CMB3D_COL_SWITCH(run_draw_zfft, buf, amp, tw, key, key_dev, s, zmask, zlo, zhi)
 }
 

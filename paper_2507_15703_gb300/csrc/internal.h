@@ -19,6 +19,7 @@ void set_error_detail(const char* msg);
 // q = m_x^2 + m_y^2 + m_z^2; tw[m] = exp(+2 pi i m / N), m < N.
 // Kernel shape variants: v in [0, num_*_variants(N)); variant 0 is the default.
 int num_col_variants(int N);
+int num_draw_variants(int N);   // draw+z shapes: the column-pass shapes, then draw-only ones
 int num_row_variants(int N);
 int num_fused_variants(int N);
 
@@ -27,7 +28,15 @@ int num_fused_variants(int N);
 // != NULL (N bits) only those whose bit is also set.
 cudaError_t launch_draw_zfft(int N, int v, float2* buf, const float* amp, const float2* tw,
                              uint64_t seed, cudaStream_t s, const uint2* key_dev = nullptr,
-                             const uint32_t* zmask = nullptr, int zlo = 0, int zhi = 0);
+                             const uint32_t* zmask = nullptr, int zlo = 0, int zhi = 0, unsigned* err = nullptr);
+
+// The draw with the z-transform as two 32-point split-FP16 DFT-GEMMs on the
+// tensor cores (N = 1024; draw variant num_draw_variants(N) - 1).  *err is set
+// if an MMA-completion wait gave up; err must not be NULL.
+bool draw_tc_supported(int N);
+cudaError_t launch_draw_tc(int N, float2* buf, const float* amp, const float2* tw, uint64_t seed, cudaStream_t s,
+                           unsigned* err, const uint2* key_dev = nullptr, const uint32_t* zmask = nullptr,
+                           int zlo = 0, int zhi = 0);
 
 // 2-D Fourier method: the hybrid layers [z][m_y][m_x'] (h <= 32 layers) from
 // the per-q table of z-covariance square roots (h x h floats per q).

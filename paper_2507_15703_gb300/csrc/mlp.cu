@@ -231,6 +231,106 @@ __global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float
   w[i] -= lr * (a / c1) / (sqrtf(b / c2) + eps);
 }
 
+// ---- refinement of a predicted P (cmb3d_mlp_refine) ------------------------
+// Minimises f(P) = 1/2 sum_l ((A P)_l / C_l - 1)^2 over P >= 0, the objective
+// of the NNLS inversion, by accelerated projected gradient (FISTA) in the
+// scaled variable y = P / s, s_j = 1 / || column j of diag(1/C) A ||.
+
+__global__ void k_ref_weights(const float* __restrict__ logc, long long n, float* __restrict__ w,
+                              float* __restrict__ w2) {
+  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float v = expf(-logc[i]);
+  w[i] = v;
+  w2[i] = v * v;
+}
+
+__global__ void k_square(const float* __restrict__ a, float* __restrict__ a2, long long n) {
+  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) a2[i] = a[i] * a[i];
+}
+
+// s = 1 / sqrt(column norms^2); the iterate starts at y = P0 / s, and x = s y = P0.
+__global__ void k_ref_start(const float* __restrict__ colsq, const float* __restrict__ logp0, long long n,
+                            float* __restrict__ sc, float* __restrict__ z, float* __restrict__ y,
+                            float* __restrict__ x) {
+  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float s = rsqrtf(fmaxf(colsq[i], 1e-30f));
+  const float p0 = expf(logp0[i]);
+  sc[i] = s;
+  z[i] = p0 / s;
+  y[i] = p0 / s;
+  x[i] = p0;
+}
+
+// The iterate back at the start (after the power iteration used y and x).
+__global__ void k_ref_reset(const float* __restrict__ logp0, const float* __restrict__ sc, long long n,
+                            float* __restrict__ z, float* __restrict__ y, float* __restrict__ x) {
+  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float p0 = expf(logp0[i]);
+  z[i] = p0 / sc[i];
+  y[i] = p0 / sc[i];
+  x[i] = p0;
+}
+
+// r = w (w ap - 1) (gradient of f with respect to A P), or with `power` w^2 ap.
+__global__ void k_ref_resid(const float* __restrict__ ap, const float* __restrict__ w, long long n, int power,
+                            float* __restrict__ r) {
+  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float wi = w[i];
+  r[i] = power ? wi * wi * ap[i] : wi * fmaf(wi, ap[i], -1.0f);
+}
+
+// One row per block: v = s g (the power-iteration image), its norm into lip[b]
+// (times 1.05) and, normalised, into y and x = s y.
+__global__ void k_ref_power(const float* __restrict__ g, const float* __restrict__ sc, int n_out,
+                            float* __restrict__ y, float* __restrict__ x, float* __restrict__ lip) {
+  __shared__ float part[256];
+  const long long o = static_cast<long long>(blockIdx.x) * n_out;
+  float acc = 0.f;
+  for (int j = threadIdx.x; j < n_out; j += blockDim.x) {
+    const float v = sc[o + j] * g[o + j];
+    acc += v * v;
+  }
+  part[threadIdx.x] = acc;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) part[threadIdx.x] += part[threadIdx.x + st];
+    __syncthreads();
+  }
+  const float nrm = sqrtf(part[0]);
+  if (threadIdx.x == 0) lip[blockIdx.x] = 1.05f * nrm;
+  const float inv = nrm > 0.f ? 1.0f / nrm : 0.f;
+  for (int j = threadIdx.x; j < n_out; j += blockDim.x) {
+    const float v = sc[o + j] * g[o + j] * inv;
+    y[o + j] = v;
+    x[o + j] = sc[o + j] * v;
+  }
+}
+
+// FISTA step: z' = max(y - s g / L, 0), y = z' + mom (z' - z), z = z', x = s y.
+__global__ void k_ref_step(const float* __restrict__ g, const float* __restrict__ sc, const float* __restrict__ lip,
+                           int n_out, long long n, float mom, float* __restrict__ z, float* __restrict__ y,
+                           float* __restrict__ x) {
+  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float s = sc[i];
+  const float zn = fmaxf(y[i] - s * g[i] / lip[i / n_out], 0.0f);
+  const float yn = fmaf(mom, zn - z[i], zn);
+  z[i] = zn;
+  y[i] = yn;
+  x[i] = s * yn;
+}
+
+__global__ void k_ref_out(const float* __restrict__ z, const float* __restrict__ sc, long long n,
+                          float* __restrict__ pk) {
+  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) pk[i] = sc[i] * z[i];
+}
+
 unsigned blocks_for(long long n, int threads = 256) { return static_cast<unsigned>((n + threads - 1) / threads); }
 
 thread_local std::string g_mlp_detail;
@@ -251,6 +351,11 @@ struct cmb3d_mlp_s {
   double* gnorm = nullptr;
   unsigned* err = nullptr;
   long long step = 0;
+  // refinement (cmb3d_mlp_refine), allocated on first use: A (.) A, and per
+  // spectrum of a chunk the weights 1/C, column scales, FISTA iterates,
+  // Lipschitz bounds and squared norms
+  float *a2 = nullptr, *rw = nullptr, *rs = nullptr, *rz = nullptr, *ry = nullptr, *rx = nullptr, *rlip = nullptr;
+  float* rnorm = nullptr;
 };
 
 namespace {
@@ -344,7 +449,9 @@ void free_mlp(cmb3d_mlp_s* h) {
                   static_cast<void*>(h->dp), static_cast<void*>(h->de), static_cast<void*>(h->dy),
                   static_cast<void*>(h->dg), static_cast<void*>(h->dz), static_cast<void*>(h->rows),
                   static_cast<void*>(h->loss), static_cast<void*>(h->err), static_cast<void*>(h->ymax),
-                  static_cast<void*>(h->gnorm)})
+                  static_cast<void*>(h->gnorm), static_cast<void*>(h->a2), static_cast<void*>(h->rw),
+                  static_cast<void*>(h->rs), static_cast<void*>(h->rz), static_cast<void*>(h->ry),
+                  static_cast<void*>(h->rx), static_cast<void*>(h->rlip), static_cast<void*>(h->rnorm)})
     cudaFree(p);
   for (float* p : h->z) cudaFree(p);
   for (float* p : h->act) cudaFree(p);
@@ -529,6 +636,71 @@ int cmb3d_mlp_params(cmb3d_mlp_t h, float* get_host, const float* set_host, int6
 }
 
 void cmb3d_mlp_destroy(cmb3d_mlp_t h) { free_mlp(h); }
+
+int cmb3d_mlp_refine(cmb3d_mlp_t h, const float* logcl_dev, const float* logpk_dev, int64_t n, int iters,
+                     int power_iters, float* pk_dev, void* stream) {
+  if (!h || n < 0 || iters < 0 || power_iters < 1 || (n > 0 && (!logcl_dev || !logpk_dev || !pk_dev)))
+    return mfail(CMB3D_EINVAL, "bad arguments");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const long long cap = h->cap, ni = h->n_in, no = h->n_out;
+  if (!h->a2) {
+    bool ok = cudaMalloc(&h->a2, ni * no * 4) == cudaSuccess && cudaMalloc(&h->rw, cap * ni * 4) == cudaSuccess &&
+              cudaMalloc(&h->rs, cap * no * 4) == cudaSuccess && cudaMalloc(&h->rz, cap * no * 4) == cudaSuccess &&
+              cudaMalloc(&h->ry, cap * no * 4) == cudaSuccess && cudaMalloc(&h->rx, cap * no * 4) == cudaSuccess &&
+              cudaMalloc(&h->rlip, cap * 4) == cudaSuccess && cudaMalloc(&h->rnorm, cap * ni * 4) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      return mfail(CMB3D_ENOMEM, "refinement buffers");
+    }
+    k_square<<<blocks_for(ni * no), 256, 0, s>>>(h->afwd, h->a2, ni * no);
+  }
+  const Mat a_t{h->afwd, no, 1};          // (n = l, k = j): A[l][j]
+  const Mat a_n{h->afwd, 1, no};          // (n = j, k = l): A[l][j]
+  for (long long b0 = 0; b0 < n; b0 += cap) {
+    const int B = static_cast<int>(std::min(cap, n - b0));
+    const long long nb_in = static_cast<long long>(B) * ni, nb_out = static_cast<long long>(B) * no;
+    const float* lc = logcl_dev + b0 * ni;
+    float* w2 = h->rnorm;
+    k_ref_weights<<<blocks_for(nb_in), 256, 0, s>>>(lc, nb_in, h->rw, w2);
+    // squared column norms of diag(1/C) A: (w^2) (A . A)
+    cudaError_t e = gemm(h, B, static_cast<int>(no), static_cast<int>(ni), Mat{w2, ni, 1}, Mat{h->a2, 1, no}, 1.f,
+                         nullptr, nullptr, h->de, no, 1, false, s);
+    if (e == cudaSuccess)
+      k_ref_start<<<blocks_for(nb_out), 256, 0, s>>>(h->de, logpk_dev + b0 * no, nb_out, h->rs, h->rz, h->ry, h->rx);
+    // Lipschitz bound of the scaled gradient: power iteration on S A^T W^2 A S
+    // from x = P0 (y and x serve as the iteration vector, then are reset)
+    for (int it = 0; it < power_iters && e == cudaSuccess; ++it) {
+      e = gemm(h, B, static_cast<int>(ni), static_cast<int>(no), Mat{h->rx, no, 1}, a_t, 1.f, nullptr, nullptr, h->p,
+               ni, 1, false, s);
+      if (e != cudaSuccess) break;
+      k_ref_resid<<<blocks_for(nb_in), 256, 0, s>>>(h->p, h->rw, nb_in, 1, h->dp);
+      e = gemm(h, B, static_cast<int>(no), static_cast<int>(ni), Mat{h->dp, ni, 1}, a_n, 1.f, nullptr, nullptr, h->de,
+               no, 1, false, s);
+      if (e != cudaSuccess) break;
+      k_ref_power<<<B, 256, 0, s>>>(h->de, h->rs, static_cast<int>(no), h->ry, h->rx, h->rlip);
+    }
+    if (e == cudaSuccess) k_ref_reset<<<blocks_for(nb_out), 256, 0, s>>>(logpk_dev + b0 * no, h->rs, nb_out, h->rz, h->ry, h->rx);
+    double t = 1.0;
+    for (int it = 0; it < iters && e == cudaSuccess; ++it) {
+      e = gemm(h, B, static_cast<int>(ni), static_cast<int>(no), Mat{h->rx, no, 1}, a_t, 1.f, nullptr, nullptr, h->p,
+               ni, 1, false, s);
+      if (e != cudaSuccess) break;
+      k_ref_resid<<<blocks_for(nb_in), 256, 0, s>>>(h->p, h->rw, nb_in, 0, h->dp);
+      e = gemm(h, B, static_cast<int>(no), static_cast<int>(ni), Mat{h->dp, ni, 1}, a_n, 1.f, nullptr, nullptr, h->de,
+               no, 1, false, s);
+      if (e != cudaSuccess) break;
+      const double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
+      k_ref_step<<<blocks_for(nb_out), 256, 0, s>>>(h->de, h->rs, h->rlip, static_cast<int>(no), nb_out,
+                                                    static_cast<float>((t - 1.0) / tn), h->rz, h->ry, h->rx);
+      t = tn;
+    }
+    if (e == cudaSuccess) k_ref_out<<<blocks_for(nb_out), 256, 0, s>>>(h->rz, h->rs, nb_out, pk_dev + b0 * no);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return mfail(CMB3D_ECUDA, cudaGetErrorString(e));
+  }
+  if (cudaStreamSynchronize(s) != cudaSuccess) return mfail(CMB3D_ECUDA, "refinement");
+  return check_err(h);
+}
 
 int cmb3d_mlp_gemm(int M, int N, int K, const float* a, int64_t as0, int64_t as1, const float* b, int64_t bs0,
                    int64_t bs1, float alpha, const float* bias, int gelu, float* out, int64_t os0, int64_t os1,

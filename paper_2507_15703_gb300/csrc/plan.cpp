@@ -384,8 +384,12 @@ int autotune(cmb3d_plan_s* p, cudaStream_t s) {
   Schedule best;
   bool ok = true;
   float t_best = 1e30f;
-  for (int v = 0; v < cmb3d::num_col_variants(N); ++v) {
-    const float t = time_launches(s, [&] { return cmb3d::launch_draw_zfft(N, v, p->buf, p->amp, p->tw, 1, s); }, &ok);
+  for (int v = 0; v < cmb3d::num_draw_variants(N); ++v) {   // timed with the plan's stored-plane range
+    const float t = time_launches(s, [&] {
+      return cmb3d::launch_draw_zfft(N, v, p->buf, p->amp, p->tw, 1, s, nullptr,
+                                     p->prune && p->zhi == 0 ? p->d_zmask : nullptr, p->prune ? p->zlo : 0,
+                                     p->prune ? p->zhi : 0, p->d_err);
+    }, &ok);
     if (!ok) return fail_cuda(cudaErrorLaunchFailure, "autotune draw_zfft");
     if (t < t_best) t_best = t, best.draw = v;
   }
@@ -430,7 +434,8 @@ int run_draw(cmb3d_plan_s* p, uint64_t seed, cudaStream_t s, float2* box, bool p
     if (p->method == 2) return cmb3d::launch_draw2d(p->N, p->h, box, p->sqt, seed, s);
     const bool pr = prune && p->prune;
     return cmb3d::launch_draw_zfft(p->N, sc.draw, box, p->amp, p->tw, seed, s, nullptr,
-                                   pr && p->zhi == 0 ? p->d_zmask : nullptr, pr ? p->zlo : 0, pr ? p->zhi : 0);
+                                   pr && p->zhi == 0 ? p->d_zmask : nullptr, pr ? p->zlo : 0, pr ? p->zhi : 0,
+                                   p->d_err);
   });
   if (e != cudaSuccess) return fail_cuda(e, "draw_zfft launch");
   return CMB3D_OK;
@@ -1440,7 +1445,7 @@ int batch_streams(const cmb3d_plan_t* plans, const uint64_t* seeds, float* const
         // with the pruned passes below, only the listed z-planes are stored
         el = cmb3d::launch_draw_zfft(N, sc.draw, p->buf, p->amp, p->tw, 0, bc.cap, bc.d_keys + b,
                                      p->prune && p->zhi == 0 ? p->d_zmask : nullptr, p->prune ? p->zlo : 0,
-                                     p->prune ? p->zhi : 0);
+                                     p->prune ? p->zhi : 0, p->d_err);
         if (el == cudaSuccess) el = cudaEventRecord(ev[static_cast<size_t>(b)], bc.cap);
         if (el == cudaSuccess) el = cudaStreamWaitEvent(bc.cap2, ev[static_cast<size_t>(b)], 0);
         if (el == cudaSuccess) {
@@ -1667,7 +1672,7 @@ int cmb3d_plan_set_schedule(cmb3d_plan_t p, const int* sched) {
   Schedule sc;
   sc.draw = sched[0];
   sc.fused = sched[3];
-  if (sc.draw < 0 || sc.draw >= cmb3d::num_col_variants(N)) return fail(CMB3D_EINVAL, "draw variant out of range");
+  if (sc.draw < 0 || sc.draw >= cmb3d::num_draw_variants(N)) return fail(CMB3D_EINVAL, "draw variant out of range");
   if (sc.fused >= 0) {
     if (sc.fused >= cmb3d::num_fused_variants(N)) return fail(CMB3D_EINVAL, "fused variant out of range");
     if (!cmb3d::fused_variant_available(N, sc.fused))

@@ -165,7 +165,8 @@ WORKLOADS = {
     "fourier2d_box512_cap20": Workload("fourier2d_box512_cap20", N=512, nside=1024,
                                        fsky=(1.0 - math.cos(math.radians(20.0))) / 2.0, lmax=768, damping=600.0,
                                        interp=3, method="2d", M=64, theta_max_deg=20.0, dp=0.0034),
-    # 1024^3 box, ~20M cap pixels, tricubic.
+    # 1024^3 box, ~20M cap pixels, tricubic; 512 k nodes keep the node
+    # spacing of the 512^3 workload's 256.
     "box1024_cap0.4_tricubic": Workload("box1024_cap0.4_tricubic", N=1024, nside=2048, fsky=0.4,
-                                        lmax=768, damping=600.0, interp=3),
+                                        lmax=768, damping=600.0, interp=3, nkbins=512),
 }
