@@ -747,7 +747,7 @@ def sweep(plan, out, stream, N, seed0, reps=20):
     import torch
     from paper_2507_15703_gb300 import cmb3d
     scheds = [(d, 0, 0, -1) for d in range(7)] + [(0, y, 0, -1) for y in range(4)] + \
-             [(0, 0, x, -1) for x in range(3)] + [(0, -1, -1, f) for f in range(4)]
+             [(0, 0, x, -1) for x in range(4)] + [(0, -1, -1, f) for f in range(4)]
     for sc in scheds:
         try:
             cmb3d.cmb3d_plan_set_schedule(plan.handle, sc)

@@ -451,6 +451,19 @@ int cmb3d_realize_sample_noalloc(int N, double L, double r, const double* pix_de
                                  const float* amp_dev, uint64_t seed, float* out_dev, void* stream);
 
 /*
+ * Test hooks (no counterpart in the paper):
+ * cmb3d_debug_alloc_limit: from now on a plan (created or growing a second
+ * box or staging buffer) whose device memory would pass `bytes` fails with
+ * CMB3D_ENOMEM, as if cudaMalloc had run out, after freeing what it took; 0
+ * removes the limit.  Process-wide, not thread-safe.
+ * cmb3d_debug_poison_boxes: waits for the plan's work, then fills its box(es)
+ * with the bit pattern 0xFFFFFFFF (NaN), so that a later map that read a box
+ * entry no pass of its own had written would come out NaN.
+ */
+void cmb3d_debug_alloc_limit(int64_t bytes);
+int cmb3d_debug_poison_boxes(cmb3d_plan_t plan);
+
+/*
  * The kernel shapes the plan uses: sched[0] = draw+z variant, sched[1] = y
  * variant, sched[2] = x variant (both -1 when fused), sched[3] = fused y+x
  * variant (-1 when separate).  Variant 0 is each kernel's default shape; with

@@ -75,6 +75,8 @@ PROTOTYPES = {
     "cmb3d_realize_samples_to_host": (_i32, [_vp, C.POINTER(_u64), _i32, C.POINTER(_vp), _vp]),
     "cmb3d_realize_sample_batch": (_i32, [C.POINTER(_vp), C.POINTER(_u64), C.POINTER(_vp), _i32, _vp]),
     "cmb3d_batch_debug": (None, [_u32, _i32, _i32]),
+    "cmb3d_debug_alloc_limit": (None, [_i64]),
+    "cmb3d_debug_poison_boxes": (_i32, [_vp]),
     "cmb3d_draw_spectrum": (_i32, [_vp, _u64, _vp, _vp]),
     "cmb3d_realize_field": (_i32, [_vp, _u64, _vp, _vp]),
     "cmb3d_philox4x32_10": (_i32, [_vp, _u64, _vp, _i64, _vp]),
@@ -326,6 +328,14 @@ def cmb3d_realize_sample_batch(plans, seeds, outs_dev, stream=None) -> None:
 
 def cmb3d_batch_debug(spin_limit: int = 0, withhold_draw: bool = False, force_form: int = -1) -> None:
     load().cmb3d_batch_debug(int(spin_limit), int(bool(withhold_draw)), int(force_form))
+
+
+def cmb3d_debug_alloc_limit(nbytes: int) -> None:
+    load().cmb3d_debug_alloc_limit(int(nbytes))
+
+
+def cmb3d_debug_poison_boxes(plan: int) -> None:
+    _check(load().cmb3d_debug_poison_boxes(plan), "cmb3d_debug_poison_boxes")
 
 
 def cmb3d_draw_spectrum(plan: int, seed: int, spec_dev, stream=None) -> None:

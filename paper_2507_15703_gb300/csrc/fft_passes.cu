@@ -100,6 +100,27 @@ __global__ void __launch_bounds__(ROWS*(N / 2 / R)) k_xc2r(float2* __restrict__ 
     xc2r_rows<N, R, ROWS, false>(buf + static_cast<size_t>(blockIdx.x) * ROWS * (N / 2), sm, tw);
 }
 
+// The same row pass compiled for MINB resident blocks per SM (register cap
+// 65536 / (MINB x threads)): more rows in flight per SM.
+template <int N, int R, int ROWS, int MINB>
+__global__ void __launch_bounds__(ROWS*(N / 2 / R), MINB) k_xc2r_mb(float2* __restrict__ buf,
+                                                                       const float2* __restrict__ tw,
+                                                                       const int32_t* __restrict__ rows) {
+  extern __shared__ float2 sm[];
+  if (rows)
+    xc2r_rows<N, R, ROWS, false>(buf, sm, tw, rows + static_cast<size_t>(blockIdx.x) * ROWS);
+  else
+    xc2r_rows<N, R, ROWS, false>(buf + static_cast<size_t>(blockIdx.x) * ROWS * (N / 2), sm, tw);
+}
+
+template <int N, int R, int ROWS, int MINB>
+constexpr auto xc2r_kernel() {
+  if constexpr (MINB > 1)
+    return k_xc2r_mb<N, R, ROWS, MINB>;
+  else
+    return k_xc2r<N, R, ROWS>;
+}
+
 // Fused y + x passes: one thread-block cluster of C blocks owns one z-plane.
 // Its blocks first transform the plane's N/2 columns along y (tiles of T
 // columns, block b taking tiles b, b+C, ...), wait at the cluster barrier, and
@@ -311,7 +332,7 @@ cudaError_t run_yfft(float2* buf, const float2* tw, cudaStream_t s, const int32_
   return cudaGetLastError();
 }
 
-template <int N, int R, int THREADS>
+template <int N, int R, int THREADS, int MINB = 1>
 cudaError_t run_xc2r(float2* buf, const float2* tw, cudaStream_t s, const int32_t* rows, int64_t nrows) {
   constexpr int N2 = N / 2, NB = N2 / R;
   constexpr int ROWS0 = THREADS / NB > 0 ? THREADS / NB : 1;
@@ -319,7 +340,7 @@ cudaError_t run_xc2r(float2* buf, const float2* tw, cudaStream_t s, const int32_
   static_assert(N < 128 || kRowListPad % ROWS == 0, "pruned row lists are padded to whole blocks of every shape");
   constexpr int P = N2 + (N2 >> 4);
   const size_t smem = sizeof(float2) * P * ROWS;
-  auto kern = k_xc2r<N, R, ROWS>;
+  auto kern = xc2r_kernel<N, R, ROWS, MINB>();
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   if (rows && (nrows <= 0 || nrows % ROWS != 0)) return nrows == 0 ? cudaSuccess : cudaErrorInvalidValue;
@@ -396,7 +417,7 @@ int num_col_variants(int N) { return N >= 2048 ? 3 : N >= 256 ? 4 : 1; }
 int num_draw_variants(int N) {
   return (N >= 1024 ? num_col_variants(N) + 2 : num_col_variants(N)) + (draw_tc_supported(N) ? 1 : 0);
 }
-int num_row_variants(int N) { return N >= 256 ? 3 : 1; }
+int num_row_variants(int N) { return N >= 512 ? 4 : N >= 256 ? 3 : 1; }
 int num_fused_variants(int N) { return N == 128 ? 1 : (N == 256 || N == 512) ? 3 : N == 1024 ? 2 : 0; }
 
 bool fused_variant_available(int N, int v) {
@@ -463,12 +484,15 @@ cudaError_t launch_xc2r(int N, int v, float2* buf, const float2* tw, cudaStream_
     case 512 * 4: return run_xc2r<512, 8, 256>(buf, tw, s, rows, nrows);
     case 512 * 4 + 1: return run_xc2r<512, 16, 256>(buf, tw, s, rows, nrows);
     case 512 * 4 + 2: return run_xc2r<512, 8, 512>(buf, tw, s, rows, nrows);
+    case 512 * 4 + 3: return run_xc2r<512, 16, 256, 4>(buf, tw, s, rows, nrows);
     case 1024 * 4: return run_xc2r<1024, 8, 256>(buf, tw, s, rows, nrows);
     case 1024 * 4 + 1: return run_xc2r<1024, 16, 256>(buf, tw, s, rows, nrows);
+    case 1024 * 4 + 3: return run_xc2r<1024, 16, 256, 4>(buf, tw, s, rows, nrows);
     case 1024 * 4 + 2: return run_xc2r<1024, 8, 512>(buf, tw, s, rows, nrows);
     case 2048 * 4: return run_xc2r<2048, 16, 256>(buf, tw, s, rows, nrows);
     case 2048 * 4 + 1: return run_xc2r<2048, 16, 512>(buf, tw, s, rows, nrows);
     case 2048 * 4 + 2: return run_xc2r<2048, 8, 512>(buf, tw, s, rows, nrows);
+    case 2048 * 4 + 3: return run_xc2r<2048, 16, 256, 4>(buf, tw, s, rows, nrows);
     default: return cudaErrorInvalidValue;
   }
 }

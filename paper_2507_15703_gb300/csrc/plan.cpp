@@ -105,6 +105,7 @@ struct cmb3d_plan_s {
   int64_t npix = 0;
   int device = 0;
   float2* buf = nullptr;          // packed half spectrum / field, 4 N^3 bytes
+  size_t box_elems = 0;           // float2 entries of buf (and buf2): the box and its scratch row
   float* amp = nullptr;           // sqrt(P_box(q)/2), q = 0 .. 3 (N/2)^2
   float2* tw = nullptr;           // exp(+2 pi i m / N), m < N
   float4* tab = nullptr;          // pixel table in gather order
@@ -184,10 +185,16 @@ struct DeviceGuard {
   }
 };
 
+// Test hook (cmb3d_debug_alloc_limit): a plan whose device memory would pass
+// this many bytes fails as if the device were out of memory (0: no limit).
+int64_t g_alloc_limit = 0;
+
 template <class T>
 int dev_alloc(cmb3d_plan_s* p, T** ptr, size_t count, const char* what) {
   *ptr = nullptr;
   if (count == 0) return CMB3D_OK;
+  if (g_alloc_limit > 0 && p->dev_bytes + static_cast<int64_t>(count * sizeof(T)) > g_alloc_limit)
+    return fail(CMB3D_ENOMEM, std::string("cudaMalloc(") + what + "): beyond the debug allocation limit");
   cudaError_t e = cudaMalloc(reinterpret_cast<void**>(ptr), count * sizeof(T));
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -394,15 +401,31 @@ int autotune(cmb3d_plan_s* p, cudaStream_t s) {
     if (t < t_best) t_best = t, best.draw = v;
   }
   float t_y = 1e30f, t_x = 1e30f, t_f = 1e30f;
+  // the y and x shapes are timed on the plane and row lists a sky map of this
+  // plan uses (the whole box when it does not prune)
   for (int v = 0; v < cmb3d::num_col_variants(N); ++v) {   // butterfly forms only: FP16 is opt-in
-    const float t = time_launches(s, [&] { return cmb3d::launch_yfft(N, v, p->buf, p->tw, s); }, &ok);
+    const float t = time_launches(s, [&] {
+      return p->prune ? cmb3d::launch_yfft(N, v, p->buf, p->tw, s, p->d_planes, static_cast<int>(p->nplanes),
+                                           p->d_rowmask)
+                      : cmb3d::launch_yfft(N, v, p->buf, p->tw, s);
+    }, &ok);
     if (!ok) return fail_cuda(cudaErrorLaunchFailure, "autotune yfft");
     if (t < t_y) t_y = t, best.y = v;
   }
   for (int v = 0; v < cmb3d::num_row_variants(N); ++v) {
-    const float t = time_launches(s, [&] { return cmb3d::launch_xc2r(N, v, p->buf, p->tw, s); }, &ok);
+    const float t = time_launches(s, [&] {
+      return p->prune ? cmb3d::launch_xc2r(N, v, p->buf, p->tw, s, p->d_rows, p->nrows_pad)
+                      : cmb3d::launch_xc2r(N, v, p->buf, p->tw, s);
+    }, &ok);
     if (!ok) return fail_cuda(cudaErrorLaunchFailure, "autotune xc2r");
     if (t < t_x) t_x = t, best.x = v;
+  }
+  // fused forms transform the whole box: compared with the separate passes on it
+  if (p->prune && !(p->flags & CMB3D_FLAG_THREE_PASS) && cmb3d::num_fused_variants(N) > 0) {
+    t_y = t_x = 0.f;
+    t_y = time_launches(s, [&] { return cmb3d::launch_yfft(N, best.y, p->buf, p->tw, s); }, &ok);
+    if (ok) t_x = time_launches(s, [&] { return cmb3d::launch_xc2r(N, best.x, p->buf, p->tw, s); }, &ok);
+    if (!ok) return fail_cuda(cudaErrorLaunchFailure, "autotune separate passes");
   }
   if (!(p->flags & CMB3D_FLAG_THREE_PASS))
     for (int v = 0; v < cmb3d::num_fused_variants(N); ++v) {
@@ -879,6 +902,7 @@ static int create_plan(cmb3d_plan_t* out, int method, int N, int M, int h, doubl
   const size_t nbuf = static_cast<size_t>(nz) * N * (N / 2) + (N / 2);   // + the scratch row
   const size_t nq = method == 2 ? 0 : 3 * static_cast<size_t>(N / 2) * (N / 2) + 1;
   int st;
+  p->box_elems = nbuf;
   if ((st = dev_alloc(p, &p->buf, nbuf, "box")) != CMB3D_OK ||
       (st = dev_alloc(p, &p->amp, nq, "amplitude table")) != CMB3D_OK ||
       (st = dev_alloc(p, &p->d_planes_all, planes_all.size(), "layer list")) != CMB3D_OK ||
@@ -1588,6 +1612,21 @@ int cmb3d_realize_sample_batch(const cmb3d_plan_t* plans, const uint64_t* seeds,
     int st = cmb3d_realize_sample(plans[b], seeds[b], outs_dev[b], stream);
     if (st != CMB3D_OK) return st;
   }
+  return CMB3D_OK;
+}
+
+void cmb3d_debug_alloc_limit(int64_t bytes) { g_alloc_limit = bytes > 0 ? bytes : 0; }
+
+int cmb3d_debug_poison_boxes(cmb3d_plan_t p) {
+  if (!p) return fail(CMB3D_EINVAL, "NULL plan");
+  DeviceGuard g(p->device);
+  cudaError_t e = drain_pipeline(p);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  const size_t bytes = p->box_elems * sizeof(float2);
+  if (e == cudaSuccess) e = cudaMemset(p->buf, 0xFF, bytes);
+  if (e == cudaSuccess && p->buf2) e = cudaMemset(p->buf2, 0xFF, bytes);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return fail_cuda(e, "poison boxes");
   return CMB3D_OK;
 }
 

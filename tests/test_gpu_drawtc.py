@@ -41,6 +41,24 @@ def rel(got, ref):
     return float(np.max(np.abs(got - ref)) / np.sqrt(np.mean(ref ** 2)))
 
 
+def test_every_1024_variant_equals_default():
+    """Every draw, y and x shape the autotuner may pick at N = 1024 (the
+    tensor-core draw included) against the default shapes (the slow oracle
+    test below pins the tensor-core draw, the y-pass study in
+    test_gpu_tensorcore the default shapes, to the FP64 oracle)."""
+    pix = cap_pixels(256, 0.4)
+    kn, pk = spectrum()
+    with cmb3d.Plan(N, L, R, pix, 3) as plan:
+        plan.set_pk(kn, pk)
+        cmb3d.cmb3d_plan_set_schedule(plan.handle, (0, 0, 0, -1))
+        ref = plan.realize_sample(21).cpu().numpy()
+        scheds = [(d, 0, 0, -1) for d in range(1, DRAW_TC + 1)] + [(0, y, 0, -1) for y in range(1, 4)] + \
+                 [(0, 0, x, -1) for x in range(1, 4)]
+        for sc in scheds:
+            cmb3d.cmb3d_plan_set_schedule(plan.handle, sc)
+            assert rel(plan.realize_sample(21).cpu().numpy(), ref) <= TOL, sc
+
+
 def test_tc_draw_is_a_draw_variant():
     pix = cap_pixels(64, 0.1)
     with cmb3d.Plan(N, L, R, pix, 3) as plan:

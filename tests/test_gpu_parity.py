@@ -154,8 +154,9 @@ def test_every_kernel_variant_matches_oracle(N):
     pix = fibonacci_sphere(20000, 6007)
     ref = orc.realize_sample(N, L, 1.0, pix, orc.p_box_of_q(N, L, kn, pk), 17, 3)
     ncol = 3 if N >= 2048 else 4                     # draw / y shapes (radix, columns per tile)
+    nrow = 4 if N >= 512 else 3                      # x shapes (radix, threads, resident blocks)
     scheds = [(d, 0, 0, -1) for d in range(ncol)] + [(0, y, 0, -1) for y in range(ncol)] + \
-             [(0, 0, x, -1) for x in range(3)] + [(0, -1, -1, f) for f in range(3)]
+             [(0, 0, x, -1) for x in range(nrow)] + [(0, -1, -1, f) for f in range(3)]
     with cmb3d.Plan(N, L, 1.0, pix, 3, cmb3d.CMB3D_FLAG_NO_PRUNE) as plan:
         plan.set_pk(kn, pk)
         for sc in scheds:
