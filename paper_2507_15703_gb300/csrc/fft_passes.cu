@@ -51,10 +51,11 @@ __global__ void __launch_bounds__(T*(N / R)) k_draw_zfft(float2* __restrict__ bu
     draw_block<N, R, T>(buf, amp, tw, key, sm, zmask, zlo, zhi);
 }
 
-// The same kernel compiled for MINB resident 256-thread blocks per SM: 4 for
-// radix 8 (64 registers a thread), 2 for radix 16 (128 registers).
+// The same kernel compiled for MINB resident blocks per SM: 256-thread tiles
+// take 4 for radix 8 (64 registers a thread) or 2 for radix 16 (128
+// registers) unless their draw variant names another count.
 template <int N, int R, int T, int MINB>
-__global__ void __launch_bounds__(256, MINB) k_draw_zfft_mb(float2* __restrict__ buf, const float* __restrict__ amp,
+__global__ void __launch_bounds__(T*(N / R), MINB) k_draw_zfft_mb(float2* __restrict__ buf, const float* __restrict__ amp,
                                                             const float2* __restrict__ tw, uint2 key,
                                                             const uint2* __restrict__ keyp,
                                                             const uint32_t* __restrict__ zmask, int zlo, int zhi) {
@@ -65,9 +66,13 @@ __global__ void __launch_bounds__(256, MINB) k_draw_zfft_mb(float2* __restrict__
     draw_block<N, R, T>(buf, amp, tw, key, sm, zmask, zlo, zhi);
 }
 
-template <int N, int R, int T>
+// MINB > 0: compiled for that many resident blocks; 0: 256-thread tiles get
+// 4 (radix 8) or 2 (radix 16), larger tiles none.
+template <int N, int R, int T, int MINB = 0>
 constexpr auto draw_kernel() {
-  if constexpr (T * (N / R) == 256)                   // 256-thread tiles: several blocks per SM
+  if constexpr (MINB > 0)
+    return k_draw_zfft_mb<N, R, T, MINB>;
+  else if constexpr (T * (N / R) == 256)
     return k_draw_zfft_mb<N, R, T, (R == 8 ? 4 : 2)>;
   else
     return k_draw_zfft<N, R, T>;
@@ -308,11 +313,11 @@ cudaError_t run_yx_dsmem(float2* buf, const float2* tw, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int N, int R, int T>
+template <int N, int R, int T, int MINB = 0>
 cudaError_t run_draw_zfft(float2* buf, const float* amp, const float2* tw, uint2 key, const uint2* keyp,
                           cudaStream_t s, const uint32_t* zmask, int zlo, int zhi) {
   const size_t smem = sizeof(float2) * col_tile_elems<N, R, T>() + sizeof(float) * draw_amp_floats<N, T>();
-  auto kern = draw_kernel<N, R, T>();
+  auto kern = draw_kernel<N, R, T, MINB>();
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   kern<<<dim3(N / 2 / T + 1, N), T * (N / R), smem, s>>>(buf, amp, tw, key, keyp, zmask, zlo, zhi > 0 ? zhi : N);
@@ -457,9 +462,13 @@ cudaError_t launch_draw_zfft(int N, int v, float2* buf, const float* amp, const 
   if (draw_tc_supported(N) && v == num_draw_variants(N) - 1)
     return launch_draw_tc(N, buf, amp, tw, seed, s, err, key_dev, zmask, zlo, zhi);
   const uint2 key = key_of(seed);
-  // draw-only shapes beyond the column-pass table: 256-thread tiles at N >= 1024
-  if (N == 1024 && v == 4) return run_draw_zfft<1024, 16, 4>(buf, amp, tw, key, key_dev, s, zmask, zlo, zhi);
-  if (N == 1024 && v == 5) return run_draw_zfft<1024, 8, 2>(buf, amp, tw, key, key_dev, s, zmask, zlo, zhi);
+  // at N = 1024 the 8-column radix-16 and the 4-column radix-8 tiles are compiled for 2
+  // resident blocks, and two draw-only 256-thread radix-16 tiles of 4 columns follow the
+  // column-pass table, compiled for 3 and for 4 resident blocks
+  if (N == 1024 && v == 1) return run_draw_zfft<1024, 16, 8, 2>(buf, amp, tw, key, key_dev, s, zmask, zlo, zhi);
+  if (N == 1024 && v == 3) return run_draw_zfft<1024, 8, 4, 2>(buf, amp, tw, key, key_dev, s, zmask, zlo, zhi);
+  if (N == 1024 && v == 4) return run_draw_zfft<1024, 16, 4, 3>(buf, amp, tw, key, key_dev, s, zmask, zlo, zhi);
+  if (N == 1024 && v == 5) return run_draw_zfft<1024, 16, 4, 4>(buf, amp, tw, key, key_dev, s, zmask, zlo, zhi);
   if (N == 2048 && v == 3) return run_draw_zfft<2048, 16, 2>(buf, amp, tw, key, key_dev, s, zmask, zlo, zhi);
   if (N == 2048 && v == 4) return run_draw_zfft<2048, 8, 1>(buf, amp, tw, key, key_dev, s, zmask, zlo, zhi);
   CMB3D_COL_SWITCH(run_draw_zfft, buf, amp, tw, key, key_dev, s, zmask, zlo, zhi)
