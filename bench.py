@@ -784,9 +784,33 @@ def oracle_map_sample(w, seed):
 ORACLE_THREADS = 1   # numpy's pocketfft and its elementwise array operations run on the calling thread
 
 
+ORACLE_BYTES_PER_CELL = 32   # peak host memory of one oracle map per box cell (31 measured at N = 64, 128)
+
+
+def host_memory_bytes():
+    """Memory this process may use: the available physical pages, capped by a
+    cgroup limit where one is set."""
+    avail = os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_AVPHYS_PAGES")
+    for f in ("/sys/fs/cgroup/memory.max", "/sys/fs/cgroup/memory/memory.limit_in_bytes"):
+        try:
+            with open(f) as fh:
+                v = fh.read().strip()
+            if v.isdigit():
+                avail = min(avail, int(v))
+        except OSError:
+            pass
+    return avail
+
+
 def cpu_baseline(w, args):
     """The oracle, as it stands, timed on one full map of the same workload on
-    the host cores (numpy FP64; one map is the bounded sample)."""
+    the host cores (numpy FP64; one map is the bounded sample).  A box whose
+    FP64 oracle map does not fit the host memory gets no baseline."""
+    need = ORACLE_BYTES_PER_CELL * w.N ** 3
+    if need > 0.6 * host_memory_bytes():
+        return {"value": None, "unit": "maps/s", "cores": ORACLE_THREADS, "kind": "oracle",
+                "sample": f"none: one FP64 oracle map of the {w.N}^3 box needs about {need / 2**30:.0f} GiB of host "
+                          f"memory, more than this host offers"}
     secs, _ = oracle_map_sample(w, 0)
     return {"value": round(1.0 / secs, 6), "unit": "maps/s", "cores": ORACLE_THREADS, "kind": "oracle",
             "sample": f"one full map of {args.workload} by the numpy FP64 oracle ({secs:.1f} s; "
@@ -801,6 +825,12 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     w = WORKLOADS[args.workload]
+    need = ORACLE_BYTES_PER_CELL * w.N ** 3
+    if need > 0.6 * host_memory_bytes():
+        print(json.dumps({"impl": "reference", "unavailable": f"one FP64 oracle map of the {w.N}^3 box needs about "
+                                                              f"{need / 2**30:.0f} GiB of host memory, more than this "
+                                                              f"host offers"}), flush=True)
+        return
     warm = max(1, min(args.warmup, 1))
     for i in range(warm):
         oracle_map_sample(w, i)
