@@ -586,6 +586,26 @@ def run_cuda_batch(args, rank, world, local, w):
     form_name = {0: f"persistent kernel ({2 - variant} blocks/SM) in a CUDA graph",
                  1: "two-stream CUDA graph (draws || passes)"}.get(form, "none")
 
+    # every batch form on the same boxes (forced; the autotuner's pick is the main line)
+    form_rates = {}
+    for force, name in ((0, "persistent_2_blocks_per_sm"), (1, "persistent_1_block_per_sm"),
+                        (2, "two_stream_graph")):
+        cmb3d.cmb3d_batch_debug(0, False, force)
+        try:
+            for i in range(2):
+                step(i)
+            torch.cuda.synchronize(dev)
+            fe0, fe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            form_steps = max(1, min(args.steps, 5))
+            fe0.record(stream)
+            for i in range(form_steps):
+                step(args.warmup + i)
+            fe1.record(stream)
+            torch.cuda.synchronize(dev)
+            form_rates[name] = round(form_steps * w.batch / (fe0.elapsed_time(fe1) / 1e3), 1)
+        finally:
+            cmb3d.cmb3d_batch_debug(0, False, -1)
+
     # the plain form for comparison: the same boxes realized one after another
     for i in range(2):
         for b, p in enumerate(plans):
@@ -611,9 +631,9 @@ def run_cuda_batch(args, rank, world, local, w):
             h.copy_(o, non_blocking=True)
         torch.cuda.synchronize(dev)
     e2e_s = max_over_ranks(dist, time.perf_counter() - t1, dev)
-    # the two-stream form runs each box's pruned transform, the persistent kernel the whole box
-    pruned = form == 1
-    extents = [cmb3d.cmb3d_plan_prune_info(p.handle) if pruned else (w.N, w.N ** 2) for p in plans]
+    # both forms run each box's pruned transform
+    pruned = True
+    extents = [cmb3d.cmb3d_plan_prune_info(p.handle) for p in plans]
     for p in plans:
         p.close()
     if rank != 0:
@@ -636,7 +656,12 @@ def run_cuda_batch(args, rank, world, local, w):
               "pruned_transform": {"z_planes_mean": round(float(np.mean([e[0] for e in extents])), 1),
                                    "rows_mean": round(float(np.mean([e[1] for e in extents])), 1),
                                    "of_planes": w.N, "of_rows": w.N ** 2},
-              "plain_form_maps_per_s": round(plain_value, 1)}
+              "plain_single_box_maps_per_s": round(plain_value, 1),
+              "plain_note": "the same boxes, one cmb3d_realize_sample call per box on the stream (pruned "
+                            "transform, same kernels: each map equals its batch map bit for bit)",
+              "forms_maps_per_s": form_rates,
+              "forms_note": "forced in turn on the same boxes, each box's pruned transform in every form; the "
+                            "main line is the autotuner's pick"}
     emit(args, w, value, t_max, world, config, batch_bytes / w.batch, kernels, "batch", maps / e2e_s,
          4 * sum(npix), 2 * args.steps, clk)
     finish_dist(dist)

@@ -12,6 +12,10 @@
 // X for every Y, G for every X (per-box completion counters).  The list
 // interleaves the ALU-bound D items of box b+1 with the memory-bound Y, X and
 // G items of box b, so both kinds of work run side by side on the GPU.
+// A box with a pruned transform (its pixels' stencils read only some z-planes
+// and rows) has D items that store only those planes, Y items over those
+// planes (storing the marked rows) and X items over those rows, as the
+// single-box passes; each box carries its own Y and X item counts.
 // Resident blocks take items in list order from an atomic counter; because
 // all blocks are resident and dependencies point backwards, every wait ends.
 // Each wait is nevertheless bounded: after `spin_limit` polls the block sets
@@ -43,14 +47,13 @@ struct Sizes {
   using S = Shape<N>;
   static constexpr int N2 = N / 2;
   static constexpr int NBX = N2 / S::RX, ROWS = kThreads / NBX, P = N2 + (N2 >> 4);
-  static constexpr int D_TILES = (N2 / S::TD) * N, Y_TILES = (N2 / S::TY) * N, X_BLOCKS = N * N / ROWS;
-  static constexpr int ND = D_TILES / kBatchTilesPerItem, NY = Y_TILES / kBatchTilesPerItem;
-  static constexpr int NX = X_BLOCKS / kBatchTilesPerItem;
+  static constexpr int D_TILES = (N2 / S::TD) * N, Y_TILES_PER_PLANE = N2 / S::TY;
+  static constexpr int ND = D_TILES / kBatchTilesPerItem;
   static constexpr int DE = col_tile_elems<N, S::RD, S::TD>(), YE = col_tile_elems<N, S::RY, S::TY>();
   static constexpr int CE = DE > YE ? DE : YE;
   static constexpr int SMEM_ELEMS = CE > ROWS * P ? CE : ROWS * P;
   static_assert(S::TD * (N / S::RD) == kThreads && S::TY * (N / S::RY) == kThreads, "tile shapes");
-  static_assert(D_TILES % kBatchTilesPerItem == 0 && X_BLOCKS % kBatchTilesPerItem == 0, "item grouping");
+  static_assert(D_TILES % kBatchTilesPerItem == 0 && kRowListPad % ROWS == 0, "item grouping, row blocks");
 };
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
@@ -70,6 +73,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_batch(const BatchBox* __rest
   extern __shared__ float2 sm[];
   __shared__ unsigned s_k;
   __shared__ int s_abort;
+  __shared__ uint32_t smask[N / 32];
   unsigned* next = ctr;
   unsigned* err = ctr + 1;
   unsigned* done = ctr + 2;
@@ -84,7 +88,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_batch(const BatchBox* __rest
     const BatchBox bx = boxes[b];
     if (type != kBatchDraw) {
       if (threadIdx.x == 0) {
-        const unsigned need = type == kBatchY ? Z::ND : type == kBatchX ? Z::NY : Z::NX;
+        const unsigned need = type == kBatchY ? static_cast<unsigned>(Z::ND) : type == kBatchX ? bx.nY : bx.nX;
         const unsigned* c = done + 4 * b + (type - 1);
         unsigned spins = 0;
         int ok = 1;
@@ -105,18 +109,30 @@ __global__ void __launch_bounds__(kThreads, MINB) k_batch(const BatchBox* __rest
       const uint2 key = make_uint2(bx.key_lo, bx.key_hi);
       for (int t = idx * kBatchTilesPerItem; t < (idx + 1) * kBatchTilesPerItem; ++t) {
         const int my = t / (N2 / S::TD), xt = t % (N2 / S::TD);
-        draw_zfft_tile<N, S::RD, S::TD>(bx.buf, bx.amp, tw, key, xt * S::TD, my, sm);
+        draw_zfft_tile<N, S::RD, S::TD>(bx.buf, bx.amp, tw, key, xt * S::TD, my, sm, bx.zmask, bx.zlo, bx.zhi);
         __syncthreads();
       }
     } else if (type == kBatchY) {
-      for (int t = idx * kBatchTilesPerItem; t < (idx + 1) * kBatchTilesPerItem; ++t) {
-        const int z = t / (N2 / S::TY), xt = t % (N2 / S::TY);
-        yfft_tile<N, S::RY, S::TY>(bx.buf + static_cast<size_t>(z) * N * N2, xt * S::TY, sm, tw);
+      const int end = min(bx.ny_tiles, (idx + 1) * kBatchTilesPerItem);
+      for (int t = idx * kBatchTilesPerItem; t < end; ++t) {
+        const int pi = t / Z::Y_TILES_PER_PLANE, xt = t % Z::Y_TILES_PER_PLANE;
+        const int z = bx.planes ? __ldg(bx.planes + pi) : pi;
+        if (bx.rowmask) {                              // the plane's stored rows, for the tile's last stage
+          for (int i = threadIdx.x; i < N / 32; i += kThreads)
+            smask[i] = __ldg(bx.rowmask + static_cast<size_t>(z) * (N / 32) + i);
+          __syncthreads();
+        }
+        yfft_tile<N, S::RY, S::TY>(bx.buf + static_cast<size_t>(z) * N * N2, xt * S::TY, sm, tw,
+                                   bx.rowmask ? smask : nullptr);
         __syncthreads();
       }
     } else if (type == kBatchX) {
-      for (int t = idx * kBatchTilesPerItem; t < (idx + 1) * kBatchTilesPerItem; ++t) {
-        xc2r_rows<N, S::RX, Z::ROWS>(bx.buf + static_cast<size_t>(t) * Z::ROWS * N2, sm, tw);
+      const int end = min(bx.nx_blocks, (idx + 1) * kBatchTilesPerItem);
+      for (int t = idx * kBatchTilesPerItem; t < end; ++t) {
+        if (bx.rows)
+          xc2r_rows<N, S::RX, Z::ROWS>(bx.buf, sm, tw, bx.rows + static_cast<size_t>(t) * Z::ROWS);
+        else
+          xc2r_rows<N, S::RX, Z::ROWS>(bx.buf + static_cast<size_t>(t) * Z::ROWS * N2, sm, tw);
         __syncthreads();
       }
     } else {
@@ -167,12 +183,15 @@ cudaError_t grid_of(int* blocks) {
 
 bool batch_supported(int N) { return N == 256 || N == 512; }
 
-void batch_item_counts(int N, int* nD, int* nY, int* nX) {
-  if (N == 256) {
-    *nD = Sizes<256>::ND, *nY = Sizes<256>::NY, *nX = Sizes<256>::NX;
-  } else {
-    *nD = Sizes<512>::ND, *nY = Sizes<512>::NY, *nX = Sizes<512>::NX;
-  }
+int batch_draw_items(int N) { return N == 256 ? Sizes<256>::ND : Sizes<512>::ND; }
+
+void batch_box_counts(int N, int64_t nplanes, int64_t nrows, int* ny_tiles, int* nx_blocks, int* nY, int* nX) {
+  const int tpp = N == 256 ? Sizes<256>::Y_TILES_PER_PLANE : Sizes<512>::Y_TILES_PER_PLANE;
+  const int rows = N == 256 ? Sizes<256>::ROWS : Sizes<512>::ROWS;
+  *ny_tiles = static_cast<int>(nplanes) * tpp;
+  *nx_blocks = static_cast<int>(nrows / rows);
+  *nY = (*ny_tiles + kBatchTilesPerItem - 1) / kBatchTilesPerItem;
+  *nX = (*nx_blocks + kBatchTilesPerItem - 1) / kBatchTilesPerItem;
 }
 
 // Variant v: 0 = two resident blocks per SM (64 registers per thread),

@@ -112,6 +112,14 @@ struct BatchBox {
   float* out;             // caller's output
   int npix;
   uint32_t key_lo, key_hi;
+  // the box's pruned transform (all NULL / whole ranges for a whole box)
+  const int32_t* planes;  // z-planes the y pass transforms, or NULL for all N
+  const uint32_t* rowmask;  // N bits per z-plane: rows the y pass stores, or NULL
+  const int32_t* rows;    // (z, y) rows the x pass transforms, or NULL for all N^2
+  const uint32_t* zmask;  // draw: N bits, planes to store when they are not one range, or NULL
+  int zlo, zhi;           // draw: store the planes zlo <= z < zhi (without zmask)
+  int ny_tiles, nx_blocks;  // y column tiles and x row blocks of this box
+  unsigned nY, nX;        // its Y and X items (what its X and G items wait for)
 };
 enum { kBatchDraw = 0, kBatchY = 1, kBatchX = 2, kBatchG = 3 };
 constexpr int kBatchTilesPerItem = 4;
@@ -121,7 +129,11 @@ inline uint64_t batch_item(int box, int type, int idx) {
   return (static_cast<uint64_t>(box) << 40) | (static_cast<uint64_t>(type) << 32) | static_cast<uint32_t>(idx);
 }
 bool batch_supported(int N);
-void batch_item_counts(int N, int* nD, int* nY, int* nX);
+// D items of a box, and the y tiles, x row blocks and Y, X items of a box
+// whose y pass covers `nplanes` z-planes and x pass `nrows` rows (a multiple of
+// kRowListPad, or N^2 for the whole box).
+int batch_draw_items(int N);
+void batch_box_counts(int N, int64_t nplanes, int64_t nrows, int* ny_tiles, int* nx_blocks, int* nY, int* nX);
 int num_batch_variants();
 cudaError_t batch_grid(int N, int interp, int v, int* blocks);
 // ctr: [0] next item, [1] error word, [2 + 4 b + type] items of (b, type) done.

@@ -1358,9 +1358,16 @@ namespace {
 // Work list of a batch: round t lists the draw items of box t interleaved, by
 // proportional position, with the y, x and gather items of box t-kLag, so the
 // draws a pass waits for were handed out a full round earlier.
+// Pruned extents of a box for the persistent kernel: (planes, rows) of its y
+// and x passes, the whole box when the plan is not pruned.
+void batch_extent(const cmb3d_plan_s* p, int* ny_tiles, int* nx_blocks, int* nY, int* nX) {
+  const int64_t N = p->N;
+  cmb3d::batch_box_counts(p->N, p->prune ? p->nplanes : N, p->prune ? p->nrows_pad : N * N, ny_tiles, nx_blocks,
+                          nY, nX);
+}
+
 std::vector<uint64_t> batch_work_list(const cmb3d_plan_t* plans, int B, int N) {
-  int nD, nY, nX;
-  cmb3d::batch_item_counts(N, &nD, &nY, &nX);
+  const int nD = cmb3d::batch_draw_items(N);
   constexpr int kLag = 2;
   std::vector<uint64_t> items;
   for (int t = 0; t < B + kLag; ++t) {
@@ -1370,6 +1377,8 @@ std::vector<uint64_t> batch_work_list(const cmb3d_plan_t* plans, int B, int N) {
     if (t >= kLag) {
       const int bx = t - kLag;
       const int nG = static_cast<int>((plans[bx]->npix + cmb3d::kBatchPixelsPerItem - 1) / cmb3d::kBatchPixelsPerItem);
+      int nyt, nxb, nY, nX;
+      batch_extent(plans[bx], &nyt, &nxb, &nY, &nX);
       for (int i = 0; i < nY; ++i) b.push_back(cmb3d::batch_item(bx, cmb3d::kBatchY, i));
       for (int i = 0; i < nX; ++i) b.push_back(cmb3d::batch_item(bx, cmb3d::kBatchX, i));
       for (int i = 0; i < nG; ++i) b.push_back(cmb3d::batch_item(bx, cmb3d::kBatchG, i));
@@ -1563,9 +1572,26 @@ int batch_persistent(const cmb3d_plan_t* plans, const uint64_t* seeds, float* co
   }
   for (int b = 0; b < B; ++b) {
     const cmb3d_plan_s* p = plans[b];
-    bc.h_boxes[static_cast<size_t>(b)] = cmb3d::BatchBox{p->buf,  p->amp, p->tab, p->perm, outs[b], static_cast<int>(p->npix),
-                                                        static_cast<uint32_t>(seeds[b] & 0xFFFFFFFFu),
-                                                        static_cast<uint32_t>(seeds[b] >> 32)};
+    cmb3d::BatchBox bb{};
+    bb.buf = p->buf;
+    bb.amp = p->amp;
+    bb.tab = p->tab;
+    bb.perm = p->perm;
+    bb.out = outs[b];
+    bb.npix = static_cast<int>(p->npix);
+    bb.key_lo = static_cast<uint32_t>(seeds[b] & 0xFFFFFFFFu);
+    bb.key_hi = static_cast<uint32_t>(seeds[b] >> 32);
+    bb.planes = p->prune ? p->d_planes : nullptr;
+    bb.rowmask = p->prune ? p->d_rowmask : nullptr;
+    bb.rows = p->prune ? p->d_rows : nullptr;
+    bb.zmask = p->prune && p->zhi == 0 ? p->d_zmask : nullptr;
+    bb.zlo = p->prune ? p->zlo : 0;
+    bb.zhi = p->prune && p->zhi > 0 ? p->zhi : N;
+    int nY, nX;
+    batch_extent(p, &bb.ny_tiles, &bb.nx_blocks, &nY, &nX);
+    bb.nY = static_cast<unsigned>(nY);
+    bb.nX = static_cast<unsigned>(nX);
+    bc.h_boxes[static_cast<size_t>(b)] = bb;
   }
   // descriptors from pageable memory: the call returns once they are staged
   if ((e = cudaMemcpyAsync(bc.d_boxes, bc.h_boxes.data(), sizeof(cmb3d::BatchBox) * B, cudaMemcpyHostToDevice, s)) !=

@@ -137,6 +137,37 @@ def test_batch_forms_agree(form):
         p.close()
 
 
+@pytest.mark.parametrize("form", [0, 2])
+def test_batch_mixes_pruned_and_whole_boxes(form):
+    """A batch of a whole-box plan (CMB3D_FLAG_NO_PRUNE) and pruned plans: each
+    box runs its own extent (planes, rows, stored draw planes) in one launch
+    and every map equals the whole-box map of its plan bit for bit."""
+    N = 256
+    kn, pk = smooth_pk(N, 2.2)
+    pixs = [cap_pixels(64, f) for f in (0.2, 0.07, 0.4)]
+    flags = [cmb3d.CMB3D_FLAG_NO_PRUNE, 0, 0]
+    plans = [cmb3d.Plan(N, 2.2, 1.0, px, 3, fl) for px, fl in zip(pixs, flags)]
+    whole = [cmb3d.Plan(N, 2.2, 1.0, px, 3, cmb3d.CMB3D_FLAG_NO_PRUNE) for px in pixs]
+    try:
+        for p, q in zip(plans, whole):
+            p.set_pk(kn, pk)
+            q.set_pk(kn, pk)
+        assert cmb3d.cmb3d_plan_prune_info(plans[1].handle)[0] < N      # pruned: fewer planes
+        outs = [torch.empty(px.shape[0], device="cuda") for px in pixs]
+        seeds = [31, 32, 33]
+        cmb3d.cmb3d_batch_debug(0, False, form)
+        try:
+            cmb3d.cmb3d_realize_sample_batch([p.handle for p in plans], seeds, outs)
+        finally:
+            cmb3d.cmb3d_batch_debug(0, False, -1)
+        for q, o, s in zip(whole, outs, seeds):
+            cmb3d.cmb3d_plan_set_schedule(q.handle, BATCH_SHAPE[N])
+            close(o.cpu().numpy(), q.realize_sample(s).cpu().numpy())
+    finally:
+        for p in plans + whole:
+            p.close()
+
+
 def test_batch_bounded_wait_times_out_and_recovers():
     N = 256
     plans, pixs, kn, pk = make_plans(N, [0.05, 0.05], 32)
