@@ -717,6 +717,9 @@ def kernel_entry(n, total_ms, all_ms, alg_bytes):
             "alg_bytes": int(alg_bytes), "alg_gbs": round(gbs, 1), "frac_of_measured_hbm": round(gbs / peak, 4)}
 
 
+ARGS_MODE: dict = {}                      # run options that change the kernels' work (set in main)
+
+
 def roofline(dom, dk, workload, peak, peak_kind, clk):
     """Roofline of the dominant kernel.  HBM-bound kernels: algorithmic bytes
     per launch / CUDA-event time against the measured copy bandwidth.  The
@@ -725,6 +728,8 @@ def roofline(dom, dk, workload, peak, peak_kind, clk):
     CUDA-event time against full issue; falls back to HBM if the counters are
     stale."""
     cnt = ncu_counters(dom, workload)
+    if cnt and any(ARGS_MODE.values()):
+        cnt = None                        # the counters were taken on the default pruned separate passes
     if dom in ALU_BOUND and cnt and cnt.get("thread_inst_per_launch"):
         p, src = alu_peak_tinst(clk)
         a = cnt["thread_inst_per_launch"] / (dk["avg_ms"] / 1e3) / 1e12
@@ -906,6 +911,7 @@ def main():
     ap.add_argument("--fp16-gemm", action="store_true",
                     help="y pass with split-FP16 DFT-GEMM stages on the tensor cores")
     args = ap.parse_args()
+    ARGS_MODE.update(no_prune=args.no_prune, fused_xg=args.fused_xg, fused=args.fused)
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
