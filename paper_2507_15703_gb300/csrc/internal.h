@@ -100,8 +100,14 @@ cudaError_t launch_xgather(int N, int interp, const float2* buf, const float2* t
                            int nentries, const int32_t* row_slot, const int32_t* row_glob, const int16_t* cols,
                            const float4* tab, const int32_t* perm, float* out, cudaStream_t s);
 
+// With `runs` (a table sorted by base cell): runs[k] = (first pixel, count) of
+// at most kGatherRun consecutive pixels sharing one base cell; each run's
+// stencil is loaded once and every pixel of the run interpolated from it, with
+// the arithmetic of the one-pixel form (maps bit for bit equal).
+constexpr int kGatherRun = 8;
 cudaError_t launch_gather(int N, int interp, const float* field, const float4* tab,
-                          const int32_t* perm, float* out, int64_t npix, cudaStream_t s);
+                          const int32_t* perm, float* out, int64_t npix, cudaStream_t s,
+                          const int2* runs = nullptr, int64_t nruns = 0);
 
 // ---- persistent batch kernel (batch.cu) ----------------------------------
 struct BatchBox {

@@ -110,6 +110,8 @@ struct cmb3d_plan_s {
   float2* tw = nullptr;           // exp(+2 pi i m / N), m < N
   float4* tab = nullptr;          // pixel table in gather order
   int32_t* perm = nullptr;        // gather order -> caller order (NULL = identity)
+  int2* d_runs = nullptr;         // sorted tables: runs (first pixel, count <= 8) of one base cell
+  int64_t nruns = 0;
   float* outbuf = nullptr;        // staging for cmb3d_realize_sample_to_host
   // cmb3d_realize_samples_to_host: a second staging buffer and a copy stream,
   // so the download of map i overlaps the kernels of map i + 1; ev_mapped[k]:
@@ -226,6 +228,7 @@ void free_plan(cmb3d_plan_s* p) {
   cudaFree(p->tw);
   cudaFree(p->tab);
   cudaFree(p->perm);
+  cudaFree(p->d_runs);
   cudaFree(p->outbuf);
   cudaFree(p->d_err);
   cudaFree(p->d_planes);
@@ -535,7 +538,8 @@ int run_gather(cmb3d_plan_s* p, float* out, cudaStream_t s, const float2* box = 
     if (p->xg)
       return cmb3d::launch_xgather(p->N, p->interp, b, p->tw, p->d_xg_entries, p->xg_nentries, p->d_xg_slot,
                                    p->d_xg_row, p->d_xg_cols, p->d_xg_tab, p->d_xg_perm, out, s);
-    return cmb3d::launch_gather(p->N, p->interp, reinterpret_cast<const float*>(b), p->tab, p->perm, out, p->npix, s);
+    return cmb3d::launch_gather(p->N, p->interp, reinterpret_cast<const float*>(b), p->tab, p->perm, out, p->npix, s,
+                                p->d_runs, p->nruns);
   });
   if (e != cudaSuccess) return fail_cuda(e, "gather launch");
   return CMB3D_OK;
@@ -779,6 +783,7 @@ static int create_plan(cmb3d_plan_t* out, int method, int N, int M, int h, doubl
   std::vector<int32_t> perm;
   std::vector<uint32_t> rowmask;
   std::vector<int32_t> planes, rows, planes_all, rows_all;
+  std::vector<int2> runs;
   bool outside = false;                               // 2-D: a stencil leaves the layers
   try {
     tab.resize(static_cast<size_t>(npix));
@@ -825,6 +830,15 @@ static int create_plan(cmb3d_plan_t* out, int method, int N, int M, int h, doubl
       for (int64_t i = 0; i < npix; ++i) {
         perm[static_cast<size_t>(i)] = order[static_cast<size_t>(i)].second;
         tab[static_cast<size_t>(i)] = raw[static_cast<size_t>(order[static_cast<size_t>(i)].second)];
+      }
+      // runs of at most kGatherRun pixels sharing one base cell (the key is the cell)
+      for (int64_t i = 0; i < npix;) {
+        int64_t j = i + 1;
+        while (j < npix && j - i < cmb3d::kGatherRun &&
+               order[static_cast<size_t>(j)].first == order[static_cast<size_t>(i)].first)
+          ++j;
+        runs.push_back(make_int2(static_cast<int>(i), static_cast<int>(j - i)));
+        i = j;
       }
     } else {
       tab.swap(raw);
@@ -912,6 +926,7 @@ static int create_plan(cmb3d_plan_t* out, int method, int N, int M, int h, doubl
       (st = dev_alloc(p, &p->outbuf, static_cast<size_t>(npix), "output staging")) != CMB3D_OK ||
       (st = dev_alloc(p, &p->d_err, 1, "error word")) != CMB3D_OK ||
       (!perm.empty() && (st = dev_alloc(p, &p->perm, perm.size(), "permutation")) != CMB3D_OK) ||
+      (!runs.empty() && (st = dev_alloc(p, &p->d_runs, runs.size(), "gather runs")) != CMB3D_OK) ||
       (!rows.empty() && ((st = dev_alloc(p, &p->d_rows, rows.size(), "row list")) != CMB3D_OK ||
                          (st = dev_alloc(p, &p->d_planes, planes.size(), "plane list")) != CMB3D_OK ||
                          (st = dev_alloc(p, &p->d_rowmask, rowmask.size(), "row mask")) != CMB3D_OK ||
@@ -925,6 +940,10 @@ static int create_plan(cmb3d_plan_t* out, int method, int N, int M, int h, doubl
     e = cudaMemcpy(p->tab, tab.data(), tab.size() * sizeof(float4), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && !perm.empty())
     e = cudaMemcpy(p->perm, perm.data(), perm.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !runs.empty()) {
+    e = cudaMemcpy(p->d_runs, runs.data(), runs.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    p->nruns = static_cast<int64_t>(runs.size());
+  }
   if (e == cudaSuccess && !rows_all.empty()) {
     e = cudaMemcpy(p->d_planes_all, planes_all.data(), planes_all.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
@@ -1497,7 +1516,7 @@ int batch_streams(const cmb3d_plan_t* plans, const uint64_t* seeds, float* const
         }
         if (el == cudaSuccess)
           el = cmb3d::launch_gather(N, p->interp, reinterpret_cast<const float*>(p->buf), p->tab, p->perm, outs[b],
-                                    p->npix, bc.cap2);
+                                    p->npix, bc.cap2, p->d_runs, p->nruns);
       }
       if (el == cudaSuccess) el = cudaEventRecord(ev[static_cast<size_t>(B) + 1], bc.cap2);
       if (el == cudaSuccess) el = cudaStreamWaitEvent(bc.cap, ev[static_cast<size_t>(B) + 1], 0);

@@ -207,6 +207,25 @@ def test_small_workload_map_matches_oracle(interp, flags):
     assert rel_err(got, ref) <= TOL
 
 
+@pytest.mark.parametrize("interp", [1, 3])
+def test_cell_run_gather_equals_one_pixel_gather(interp):
+    """A sorted table is gathered in runs of up to 8 pixels of one base cell
+    (the cell's stencil loaded once); the unsorted table one pixel per thread.
+    Dense pixels (about 31 per cell, so runs are cut at 8, ragged ends) over
+    the whole sphere with L = 2r, so stencils wrap in x, y and z: the maps
+    must be equal bit for bit."""
+    N, L, r = 64, 2.0, 1.0
+    kn, pk = smooth_pk(N, L)
+    pix = fibonacci_sphere(400003)
+    flags = cmb3d.CMB3D_FLAG_ALLOW_WRAP
+    with cmb3d.Plan(N, L, r, pix, interp, flags) as a, \
+            cmb3d.Plan(N, L, r, pix, interp, flags | cmb3d.CMB3D_FLAG_NO_SORT) as b:
+        a.set_pk(kn, pk)
+        b.set_pk(kn, pk)
+        for seed in (5, 6):
+            np.testing.assert_array_equal(a.realize_sample(seed).cpu().numpy(), b.realize_sample(seed).cpu().numpy())
+
+
 @pytest.mark.parametrize("N,npix,interp", [(128, 3001, 3), (256, 70001, 1), (8, 257, 3)])
 def test_ragged_maps_match_oracle(N, npix, interp):
     L, r = 2.2, 1.0
