@@ -192,7 +192,7 @@ def b_alg_bytes(N: int, npix: int) -> int:
 
 
 def algorithmic_bytes(N: int, npix: int, planes: int | None = None, rows: int | None = None,
-                      nz: int | None = None, draw_planes: int | None = None) -> dict:
+                      nz: int | None = None, draw_planes: int | None = None, x_stored: int | None = None) -> dict:
     """Bytes each kernel must move per launch (the packed half spectrum and the
     real field are both 4 N^2 nz bytes for nz z-planes, N for the 3-D box and
     h layers for the 2-D method; a row is 4 N bytes): the draw writes the
@@ -200,13 +200,15 @@ def algorithmic_bytes(N: int, npix: int, planes: int | None = None, rows: int | 
     writes its rows; xc2r reads and writes its rows; gather reads 16 B of table
     + 4 B of permutation per pixel and writes 4 B per pixel (field reads are
     cache-dependent and not counted).  planes, rows: the pruned extent of the
-    sky-map path (default: whole box)."""
+    sky-map path (default: whole box); x_stored: the reals the x pass writes
+    back (the column blocks the stencils read; default: whole rows)."""
     nz = N if nz is None else nz
     box, row = 4 * N * N * nz, 4 * N
     planes = nz if planes is None else planes
     rows = nz * N if rows is None else rows
     drawn = 4 * N * N * (nz if draw_planes is None else draw_planes)
-    return {"draw_zfft": drawn, "yfft": planes * N * row + rows * row, "xc2r": 2 * rows * row,
+    x_write = rows * row if x_stored is None else 4 * x_stored
+    return {"draw_zfft": drawn, "yfft": planes * N * row + rows * row, "xc2r": rows * row + x_write,
             "gather": 24 * npix, "yx_fused": 2 * box}
 
 
@@ -298,6 +300,7 @@ def run_cuda(args, rank, world, local):
     stage_ms, stage_n = cmb3d.cmb3d_stage_times(plan.handle, reset=True)
     t_max = max_over_ranks(dist, ms, dev)
     n_planes, n_rows = cmb3d.cmb3d_plan_prune_info(plan.handle)
+    x_stored = cmb3d.cmb3d_plan_x_stored(plan.handle)
 
     # end to end through the host-output entry point: every map copied to
     # pinned host memory (a ring of 4 buffers), each download overlapping the
@@ -363,7 +366,8 @@ def run_cuda(args, rank, world, local):
     value = job_throughput(world, args.steps, t_max)
     # the 3-D draw stores only the z-planes the pruned y pass reads; the 2-D
     # draw writes all its layers
-    ab = algorithmic_bytes(w.N, npix, n_planes, n_rows, nlayers, nlayers if w.method == "2d" else n_planes)
+    ab = algorithmic_bytes(w.N, npix, n_planes, n_rows, nlayers, nlayers if w.method == "2d" else n_planes,
+                           x_stored if not args.fused_xg else None)
     names = cmb3d.STAGE_NAMES
     kernels = {}
     for i, name in enumerate(names):
@@ -380,9 +384,11 @@ def run_cuda(args, rank, world, local):
                            "restriction": "three-pass" if args.three_pass else "fused" if args.fused else "autotuned",
                            "y_pass": "split-FP16 DFT-GEMM (tcgen05)" if args.fp16_gemm else "FP32 butterflies",
                            "pipelined": bool(args.pipeline), "fused_x_gather": bool(args.fused_xg)},
-              "pruned_transform": {"z_planes": n_planes, "rows": n_rows, "of_planes": w.N, "of_rows": w.N ** 2,
+              "pruned_transform": {"z_planes": n_planes, "rows": n_rows, "x_stored_reals": x_stored,
+                                   "of_planes": w.N, "of_rows": w.N ** 2,
                                    "note": "y pass on the z-planes, x pass on the (z, y) rows the "
-                                           "interpolation stencils read; maps equal the whole-box maps bit for bit"},
+                                           "interpolation stencils read, storing only the column blocks they "
+                                           "read; maps equal the whole-box maps bit for bit"},
               "l2": f"no flush: per-map working set {per_map_bytes / 2**30:.2f} GiB > 129 MiB L2",
               "cl_fit_max_rel_err": fit_err,
               "cl_fit_rms_rel_err": None if learned is not None else round(fit_rms, 4),
@@ -633,7 +639,7 @@ def run_cuda_batch(args, rank, world, local, w):
     e2e_s = max_over_ranks(dist, time.perf_counter() - t1, dev)
     # both forms run each box's pruned transform
     pruned = True
-    extents = [cmb3d.cmb3d_plan_prune_info(p.handle) for p in plans]
+    extents = [cmb3d.cmb3d_plan_prune_info(p.handle) + (cmb3d.cmb3d_plan_x_stored(p.handle),) for p in plans]
     for p in plans:
         p.close()
     if rank != 0:
@@ -642,8 +648,8 @@ def run_cuda_batch(args, rank, world, local, w):
     maps = world * args.steps * w.batch
     value = job_throughput(world, args.steps * w.batch, t_max)
     batch_bytes = 24 * sum(npix)
-    for zp, rw in extents:
-        ab = algorithmic_bytes(w.N, 0, zp, rw, None, zp if pruned else None)   # pruned draws store zp planes
+    for zp, rw, xs in extents:
+        ab = algorithmic_bytes(w.N, 0, zp, rw, None, zp if pruned else None, xs)   # pruned draws store zp planes
         batch_bytes += ab["draw_zfft"] + ab["yfft"] + ab["xc2r"]
     kernels = {"batch": kernel_entry(args.steps, ms, ms, batch_bytes)}
     kernels["batch"]["note"] = "one step = the whole batch (persistent kernel or graph), CUDA events"

@@ -585,6 +585,14 @@ int cmb3d_plan_info(cmb3d_plan_t plan, int* N, int64_t* npix, int64_t* device_by
  */
 int cmb3d_plan_prune_info(cmb3d_plan_t plan, int64_t* planes, int64_t* rows);
 
+/*
+ * Reals the x pass of a sky map stores: for each row it covers, only the
+ * column blocks (N/32 columns each) that the pixels' interpolation stencils
+ * read are written back (the gather reads nothing else).  N^3 (N^2 h for the
+ * 2-D method) without pruning.  *reals: host pointer.
+ */
+int cmb3d_plan_x_stored(cmb3d_plan_t plan, int64_t* reals);
+
 /* Release the plan and all device memory it owns (NULL is ignored). */
 void cmb3d_destroy(cmb3d_plan_t plan);
 

@@ -84,6 +84,7 @@ PROTOTYPES = {
     "cmb3d_realize_sample_noalloc": (_i32, [_i32, C.c_double, C.c_double, _vp, _i64, _i32, _vp, _u64, _vp, _vp]),
     "cmb3d_plan_info": (_i32, [_vp, C.POINTER(_i32), C.POINTER(_i64), C.POINTER(_i64)]),
     "cmb3d_plan_prune_info": (_i32, [_vp, C.POINTER(_i64), C.POINTER(_i64)]),
+    "cmb3d_plan_x_stored": (_i32, [_vp, C.POINTER(_i64)]),
     "cmb3d_plan_schedule": (_i32, [_vp, C.POINTER(_i32)]),
     "cmb3d_batch_schedule": (_i32, [_vp, C.POINTER(_i32), C.POINTER(_i32)]),
     "cmb3d_plan_set_schedule": (_i32, [_vp, C.POINTER(_i32)]),
@@ -383,6 +384,14 @@ def cmb3d_plan_info(plan: int) -> tuple[int, int, int]:
     n, npix, nbytes = _i32(), _i64(), _i64()
     _check(lib.cmb3d_plan_info(plan, C.byref(n), C.byref(npix), C.byref(nbytes)), "cmb3d_plan_info")
     return n.value, npix.value, nbytes.value
+
+
+def cmb3d_plan_x_stored(plan: int) -> int:
+    """Reals the x pass of a sky map stores (the column blocks the stencils read)."""
+    lib = load()
+    reals = _i64()
+    _check(lib.cmb3d_plan_x_stored(plan, C.byref(reals)), "cmb3d_plan_x_stored")
+    return reals.value
 
 
 def cmb3d_plan_prune_info(plan: int) -> tuple[int, int]:

@@ -130,7 +130,8 @@ __global__ void __launch_bounds__(kThreads, MINB) k_batch(const BatchBox* __rest
       const int end = min(bx.nx_blocks, (idx + 1) * kBatchTilesPerItem);
       for (int t = idx * kBatchTilesPerItem; t < end; ++t) {
         if (bx.rows)
-          xc2r_rows<N, S::RX, Z::ROWS>(bx.buf, sm, tw, bx.rows + static_cast<size_t>(t) * Z::ROWS);
+          xc2r_rows<N, S::RX, Z::ROWS>(bx.buf, sm, tw, bx.rows + static_cast<size_t>(t) * Z::ROWS,
+                                       bx.cols ? bx.cols + static_cast<size_t>(t) * Z::ROWS : nullptr);
         else
           xc2r_rows<N, S::RX, Z::ROWS>(bx.buf + static_cast<size_t>(t) * Z::ROWS * N2, sm, tw);
         __syncthreads();

@@ -97,10 +97,12 @@ __global__ void __launch_bounds__(T*(N / R)) k_yfft(float2* __restrict__ buf, co
 
 template <int N, int R, int ROWS>
 __global__ void __launch_bounds__(ROWS*(N / 2 / R)) k_xc2r(float2* __restrict__ buf, const float2* __restrict__ tw,
-                                                              const int32_t* __restrict__ rows) {
+                                                              const int32_t* __restrict__ rows,
+                                                              const uint32_t* __restrict__ cols) {
   extern __shared__ float2 sm[];
   if (rows)
-    xc2r_rows<N, R, ROWS, false>(buf, sm, tw, rows + static_cast<size_t>(blockIdx.x) * ROWS);
+    xc2r_rows<N, R, ROWS, false>(buf, sm, tw, rows + static_cast<size_t>(blockIdx.x) * ROWS,
+                                 cols ? cols + static_cast<size_t>(blockIdx.x) * ROWS : nullptr);
   else
     xc2r_rows<N, R, ROWS, false>(buf + static_cast<size_t>(blockIdx.x) * ROWS * (N / 2), sm, tw);
 }
@@ -110,10 +112,12 @@ __global__ void __launch_bounds__(ROWS*(N / 2 / R)) k_xc2r(float2* __restrict__ 
 template <int N, int R, int ROWS, int MINB>
 __global__ void __launch_bounds__(ROWS*(N / 2 / R), MINB) k_xc2r_mb(float2* __restrict__ buf,
                                                                        const float2* __restrict__ tw,
-                                                                       const int32_t* __restrict__ rows) {
+                                                                       const int32_t* __restrict__ rows,
+                                                                       const uint32_t* __restrict__ cols) {
   extern __shared__ float2 sm[];
   if (rows)
-    xc2r_rows<N, R, ROWS, false>(buf, sm, tw, rows + static_cast<size_t>(blockIdx.x) * ROWS);
+    xc2r_rows<N, R, ROWS, false>(buf, sm, tw, rows + static_cast<size_t>(blockIdx.x) * ROWS,
+                                 cols ? cols + static_cast<size_t>(blockIdx.x) * ROWS : nullptr);
   else
     xc2r_rows<N, R, ROWS, false>(buf + static_cast<size_t>(blockIdx.x) * ROWS * (N / 2), sm, tw);
 }
@@ -338,7 +342,8 @@ cudaError_t run_yfft(float2* buf, const float2* tw, cudaStream_t s, const int32_
 }
 
 template <int N, int R, int THREADS, int MINB = 1>
-cudaError_t run_xc2r(float2* buf, const float2* tw, cudaStream_t s, const int32_t* rows, int64_t nrows) {
+cudaError_t run_xc2r(float2* buf, const float2* tw, cudaStream_t s, const int32_t* rows, int64_t nrows,
+                     const uint32_t* cols) {
   constexpr int N2 = N / 2, NB = N2 / R;
   constexpr int ROWS0 = THREADS / NB > 0 ? THREADS / NB : 1;
   constexpr int ROWS = ROWS0 < N * N ? ROWS0 : N * N;
@@ -350,7 +355,7 @@ cudaError_t run_xc2r(float2* buf, const float2* tw, cudaStream_t s, const int32_
   if (e != cudaSuccess) return e;
   if (rows && (nrows <= 0 || nrows % ROWS != 0)) return nrows == 0 ? cudaSuccess : cudaErrorInvalidValue;
   const int64_t nb = rows ? nrows / ROWS : static_cast<int64_t>(N) * N / ROWS;
-  kern<<<dim3(static_cast<unsigned>(nb)), ROWS * NB, smem, s>>>(buf, tw, rows);
+  kern<<<dim3(static_cast<unsigned>(nb)), ROWS * NB, smem, s>>>(buf, tw, rows, rows ? cols : nullptr);
   return cudaGetLastError();
 }
 
@@ -480,28 +485,28 @@ cudaError_t launch_yfft(int N, int v, float2* buf, const float2* tw, cudaStream_
 }
 
 cudaError_t launch_xc2r(int N, int v, float2* buf, const float2* tw, cudaStream_t s, const int32_t* rows,
-                        int64_t nrows) {
+                        int64_t nrows, const uint32_t* cols) {
   switch (N * 4 + v) {
-    case 8 * 4: return run_xc2r<8, 4, 256>(buf, tw, s, rows, nrows);
-    case 16 * 4: return run_xc2r<16, 8, 256>(buf, tw, s, rows, nrows);
-    case 32 * 4: return run_xc2r<32, 8, 256>(buf, tw, s, rows, nrows);
-    case 64 * 4: return run_xc2r<64, 8, 256>(buf, tw, s, rows, nrows);
-    case 128 * 4: return run_xc2r<128, 8, 256>(buf, tw, s, rows, nrows);
-    case 256 * 4: return run_xc2r<256, 8, 256>(buf, tw, s, rows, nrows);
-    case 256 * 4 + 1: return run_xc2r<256, 16, 256>(buf, tw, s, rows, nrows);
-    case 256 * 4 + 2: return run_xc2r<256, 8, 512>(buf, tw, s, rows, nrows);
-    case 512 * 4: return run_xc2r<512, 8, 256>(buf, tw, s, rows, nrows);
-    case 512 * 4 + 1: return run_xc2r<512, 16, 256>(buf, tw, s, rows, nrows);
-    case 512 * 4 + 2: return run_xc2r<512, 8, 512>(buf, tw, s, rows, nrows);
-    case 512 * 4 + 3: return run_xc2r<512, 16, 256, 4>(buf, tw, s, rows, nrows);
-    case 1024 * 4: return run_xc2r<1024, 8, 256>(buf, tw, s, rows, nrows);
-    case 1024 * 4 + 1: return run_xc2r<1024, 16, 256>(buf, tw, s, rows, nrows);
-    case 1024 * 4 + 3: return run_xc2r<1024, 16, 256, 4>(buf, tw, s, rows, nrows);
-    case 1024 * 4 + 2: return run_xc2r<1024, 8, 512>(buf, tw, s, rows, nrows);
-    case 2048 * 4: return run_xc2r<2048, 16, 256>(buf, tw, s, rows, nrows);
-    case 2048 * 4 + 1: return run_xc2r<2048, 16, 512>(buf, tw, s, rows, nrows);
-    case 2048 * 4 + 2: return run_xc2r<2048, 8, 512>(buf, tw, s, rows, nrows);
-    case 2048 * 4 + 3: return run_xc2r<2048, 16, 256, 4>(buf, tw, s, rows, nrows);
+    case 8 * 4: return run_xc2r<8, 4, 256>(buf, tw, s, rows, nrows, cols);
+    case 16 * 4: return run_xc2r<16, 8, 256>(buf, tw, s, rows, nrows, cols);
+    case 32 * 4: return run_xc2r<32, 8, 256>(buf, tw, s, rows, nrows, cols);
+    case 64 * 4: return run_xc2r<64, 8, 256>(buf, tw, s, rows, nrows, cols);
+    case 128 * 4: return run_xc2r<128, 8, 256>(buf, tw, s, rows, nrows, cols);
+    case 256 * 4: return run_xc2r<256, 8, 256>(buf, tw, s, rows, nrows, cols);
+    case 256 * 4 + 1: return run_xc2r<256, 16, 256>(buf, tw, s, rows, nrows, cols);
+    case 256 * 4 + 2: return run_xc2r<256, 8, 512>(buf, tw, s, rows, nrows, cols);
+    case 512 * 4: return run_xc2r<512, 8, 256>(buf, tw, s, rows, nrows, cols);
+    case 512 * 4 + 1: return run_xc2r<512, 16, 256>(buf, tw, s, rows, nrows, cols);
+    case 512 * 4 + 2: return run_xc2r<512, 8, 512>(buf, tw, s, rows, nrows, cols);
+    case 512 * 4 + 3: return run_xc2r<512, 16, 256, 4>(buf, tw, s, rows, nrows, cols);
+    case 1024 * 4: return run_xc2r<1024, 8, 256>(buf, tw, s, rows, nrows, cols);
+    case 1024 * 4 + 1: return run_xc2r<1024, 16, 256>(buf, tw, s, rows, nrows, cols);
+    case 1024 * 4 + 3: return run_xc2r<1024, 16, 256, 4>(buf, tw, s, rows, nrows, cols);
+    case 1024 * 4 + 2: return run_xc2r<1024, 8, 512>(buf, tw, s, rows, nrows, cols);
+    case 2048 * 4: return run_xc2r<2048, 16, 256>(buf, tw, s, rows, nrows, cols);
+    case 2048 * 4 + 1: return run_xc2r<2048, 16, 512>(buf, tw, s, rows, nrows, cols);
+    case 2048 * 4 + 2: return run_xc2r<2048, 8, 512>(buf, tw, s, rows, nrows, cols);
+    case 2048 * 4 + 3: return run_xc2r<2048, 16, 256, 4>(buf, tw, s, rows, nrows, cols);
     default: return cudaErrorInvalidValue;
   }
 }

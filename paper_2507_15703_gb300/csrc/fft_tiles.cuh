@@ -125,6 +125,7 @@ __device__ __forceinline__ void draw_zfft_tile(float2* __restrict__ buf, const f
                                                float2* sm, const uint32_t* __restrict__ zmask = nullptr,
                                                int zlo = 0, int zhi = N) {
   constexpr int N2 = N / 2, NB = N / R, H = N / 2;
+  static_assert(R < 32, "one bit per output of a thread");
   const int c = threadIdx.x % T, j = threadIdx.x / T;
   float2 v[R];
   float2* col;
@@ -171,10 +172,25 @@ __device__ __forceinline__ void draw_zfft_tile(float2* __restrict__ buf, const f
     for (int r = 0; r < R / 2; ++r) draw_packed_pair<N>(xp, my, j + r * NB, amp, key, v[r], v[r + R / 2]);
     col = buf + static_cast<size_t>(my) * N2 + xp;
   }
+  // The thread's outputs are n = j + k NB for k < R (in the engine's output
+  // order), so the stored range zlo <= n < zhi is one run of k.  From radix 16
+  // one mask per thread replaces two compares per output (measured: fewer
+  // lane-instructions at radix 16, more at radix 8, where a thread has only
+  // eight outputs to spread the mask over).
+  uint32_t kmask = 0u;
+  if constexpr (R >= 16) {
+    const int klo = min(R, max(0, (zlo - j + NB - 1) / NB)), khi = min(R, max(0, (zhi - j + NB - 1) / NB));
+    kmask = store ? (((1u << khi) - 1u) & ~((1u << klo) - 1u)) : 0u;
+  }
   stockham<N, R, N, false>(
       v, sm, tw, j, [&](int n) { return col_slot<R, T>(n, c); },
       [&](int n, float2 x) {
-        if (store && n >= zlo && n < zhi && (!zmask || ((__ldg(zmask + (n >> 5)) >> (n & 31)) & 1u)))
+        bool in_range;
+        if constexpr (R >= 16)
+          in_range = (kmask >> ((n - j) / NB)) & 1u;
+        else
+          in_range = store && n >= zlo && n < zhi;
+        if (in_range && (!zmask || ((__ldg(zmask + (n >> 5)) >> (n & 31)) & 1u)))
           col[static_cast<size_t>(n) * N * N2] = x;
       },
       BlockSync{});
@@ -261,14 +277,30 @@ __device__ __forceinline__ void xc2r_row_transform(const float2* g, float2* sm,
 }
 
 // The block's rows are rows[0 .. ROWS-1] (consecutive), or with `list` the rows
-// rows + list[rl] * N/2 for rl < ROWS; each is transformed in place.
+// rows + list[rl] * N/2 for rl < ROWS; each is transformed in place.  With
+// `cols` (one word per listed row) an entry n, the reals 2n and 2n + 1, is
+// stored only when bit 2n / (N/32) of the row's word is set.
 template <int N, int R, int ROWS, bool FIRST_SYNC = true>
 __device__ __forceinline__ void xc2r_rows(float2* __restrict__ rows, float2* sm, const float2* __restrict__ tw,
-                                          const int32_t* __restrict__ list = nullptr) {
+                                          const int32_t* __restrict__ list = nullptr,
+                                          const uint32_t* __restrict__ cols = nullptr) {
   constexpr int N2 = N / 2, NB = N2 / R;
-  const int rl = threadIdx.x / NB;
+  constexpr int CSH = ilog2c(N) - 5 > 0 ? ilog2c(N) - 5 : 0;   // column blocks of N/32 reals
+  static_assert(32 % R == 0, "whole column blocks per output step");
+  const int rl = threadIdx.x / NB, j = threadIdx.x % NB;
   float2* g = rows + static_cast<size_t>(list ? __ldg(list + rl) : rl) * N2;
-  xc2r_row_transform<N, R, ROWS, FIRST_SYNC>(g, sm, tw, [&](int n, float2 x) { g[n] = x; });
+  if (list) {
+    // the thread's outputs are n = j + k NB (k < R): entry n holds reals 2n, 2n+1
+    // of block (2 j >> CSH) + k 32/R, since 2 k NB = k N/R is a whole number
+    // of blocks; so the row's word is shifted once and each output tests one
+    // fixed bit (one transform instance for listed rows, with or without cols)
+    const uint32_t cmj = cols ? __ldg(cols + rl) >> ((2 * j) >> CSH) : ~0u;
+    xc2r_row_transform<N, R, ROWS, FIRST_SYNC>(g, sm, tw, [&](int n, float2 x) {
+      if ((cmj >> (((n - j) / NB) * (32 / R))) & 1u) g[n] = x;
+    });
+  } else {
+    xc2r_row_transform<N, R, ROWS, FIRST_SYNC>(g, sm, tw, [&](int n, float2 x) { g[n] = x; });
+  }
 }
 
 }  // namespace cmb3d

@@ -68,10 +68,14 @@ cudaError_t launch_yfft_gemm(int N, float2* buf, const float2* tw, unsigned* err
 // With `rows` (row indices z N + y, nrows a multiple of the shape's rows per
 // block: kRowListPad covers every shape for N >= 128, kRowListPadAny every N)
 // only the listed rows are transformed; padding entries must name a scratch row.
+constexpr int ilog2i(int n) { return n <= 1 ? 0 : 1 + ilog2i(n >> 1); }
 constexpr int kRowListPad = 64;
 constexpr int kRowListPadAny = 256;
+// With `cols` (one word per listed row) the transformed row is stored only in
+// the column blocks whose bit is set, block b holding columns [b N/32, (b+1) N/32):
+// the blocks the interpolation stencils of a sky map read.
 cudaError_t launch_xc2r(int N, int v, float2* buf, const float2* tw, cudaStream_t s, const int32_t* rows = nullptr,
-                        int64_t nrows = 0);
+                        int64_t nrows = 0, const uint32_t* cols = nullptr);
 
 // Interpolate the field float[z][y][x] at npix pixels.  tab[i] = (tx, ty, tz,
 // packed base cell) in gather order; out[perm[i]] receives pixel i (perm may
@@ -122,6 +126,7 @@ struct BatchBox {
   const int32_t* planes;  // z-planes the y pass transforms, or NULL for all N
   const uint32_t* rowmask;  // N bits per z-plane: rows the y pass stores, or NULL
   const int32_t* rows;    // (z, y) rows the x pass transforms, or NULL for all N^2
+  const uint32_t* cols;   // per listed row, the column blocks to store (see launch_xc2r), or NULL
   const uint32_t* zmask;  // draw: N bits, planes to store when they are not one range, or NULL
   int zlo, zhi;           // draw: store the planes zlo <= z < zhi (without zmask)
   int ny_tiles, nx_blocks;  // y column tiles and x row blocks of this box

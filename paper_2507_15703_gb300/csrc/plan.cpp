@@ -138,6 +138,8 @@ struct cmb3d_plan_s {
   int32_t* d_planes = nullptr;
   int32_t* d_rows = nullptr;
   uint32_t* d_rowmask = nullptr;   // N bits per z-plane
+  uint32_t* d_rowcols = nullptr;   // per listed row: the column blocks (N/32 columns each) the stencils read
+  int64_t x_stored = 0;            // reals the pruned x pass stores (set column blocks x N/32)
   uint32_t* d_zmask = nullptr;     // N bits: the listed z-planes (the draw stores only these for maps)
   int zlo = 0, zhi = 0;            // listed z-planes as one range [zlo, zhi) when contiguous (then no mask)
   // CMB3D_FLAG_PIPELINE: a second box and two internal streams; the draw of a
@@ -234,6 +236,7 @@ void free_plan(cmb3d_plan_s* p) {
   cudaFree(p->d_planes);
   cudaFree(p->d_rows);
   cudaFree(p->d_rowmask);
+  cudaFree(p->d_rowcols);
   cudaFree(p->d_zmask);
   cudaFree(p->sqt);
   cudaFree(p->d_planes_all);
@@ -417,7 +420,7 @@ int autotune(cmb3d_plan_s* p, cudaStream_t s) {
   }
   for (int v = 0; v < cmb3d::num_row_variants(N); ++v) {
     const float t = time_launches(s, [&] {
-      return p->prune ? cmb3d::launch_xc2r(N, v, p->buf, p->tw, s, p->d_rows, p->nrows_pad)
+      return p->prune ? cmb3d::launch_xc2r(N, v, p->buf, p->tw, s, p->d_rows, p->nrows_pad, p->d_rowcols)
                       : cmb3d::launch_xc2r(N, v, p->buf, p->tw, s);
     }, &ok);
     if (!ok) return fail_cuda(cudaErrorLaunchFailure, "autotune xc2r");
@@ -486,7 +489,7 @@ int run_passes(cmb3d_plan_s* p, cudaStream_t s, bool prune, float2* box) {
     if (no_x) return CMB3D_OK;
     e = timed(p, CMB3D_STAGE_XC2R, s, [&] {
       return cmb3d::launch_xc2r(p->N, xv, box, p->tw, s, pr ? p->d_rows : p->d_rows_all,
-                                pr ? p->nrows_pad : p->nrows_all_pad);
+                                pr ? p->nrows_pad : p->nrows_all_pad, pr ? p->d_rowcols : nullptr);
     });
     if (e != cudaSuccess) return fail_cuda(e, "xc2r launch");
     return CMB3D_OK;
@@ -500,7 +503,7 @@ int run_passes(cmb3d_plan_s* p, cudaStream_t s, bool prune, float2* box) {
     if (e != cudaSuccess) return fail_cuda(e, "yfft launch");
     if (no_x) return CMB3D_OK;
     e = timed(p, CMB3D_STAGE_XC2R, s,
-              [&] { return cmb3d::launch_xc2r(p->N, xv, box, p->tw, s, p->d_rows, p->nrows_pad); });
+              [&] { return cmb3d::launch_xc2r(p->N, xv, box, p->tw, s, p->d_rows, p->nrows_pad, p->d_rowcols); });
     if (e != cudaSuccess) return fail_cuda(e, "xc2r launch");
     return CMB3D_OK;
   }
@@ -784,6 +787,8 @@ static int create_plan(cmb3d_plan_t* out, int method, int N, int M, int h, doubl
   std::vector<uint32_t> rowmask;
   std::vector<int32_t> planes, rows, planes_all, rows_all;
   std::vector<int2> runs;
+  std::vector<uint32_t> colmask, rowcols;           // column blocks the stencils read, per row / per listed row
+  int64_t x_stored = 0;
   bool outside = false;                               // 2-D: a stencil leaves the layers
   try {
     tab.resize(static_cast<size_t>(npix));
@@ -849,11 +854,25 @@ static int create_plan(cmb3d_plan_t* out, int method, int N, int M, int h, doubl
     const size_t words = static_cast<size_t>(N) * N / 32;
     if (!(flags & CMB3D_FLAG_NO_PRUNE) && N >= 128 && npix > 0) {
       rowmask.assign(words, 0u);
+      colmask.assign(static_cast<size_t>(nz) * N, 0u);
+      const int csh = cmb3d::ilog2i(N) - 5;            // column block: N / 32 columns
       uint64_t prev = ~uint64_t(0);
+      uint32_t cur = 0;                               // column blocks of the current (z, y) group
+      auto flush = [&](uint64_t key) {
+        const int bz = static_cast<int>(key / static_cast<uint64_t>(N)), by = static_cast<int>(key % N);
+        for (int c = 0; c < K; ++c) {
+          const int z = (bz + c + OFF + N) & (N - 1);
+          if (z >= nz) continue;
+          for (int b = 0; b < K; ++b)
+            colmask[static_cast<size_t>(z) * N + static_cast<size_t>((by + b + OFF + N) & (N - 1))] |= cur;
+        }
+      };
       for (int64_t i = 0; i < npix; ++i) {
         uint64_t key;
+        int bx;
         if (sort) {
           key = order[static_cast<size_t>(i)].first / static_cast<uint64_t>(N);
+          bx = static_cast<int>(order[static_cast<size_t>(i)].first % static_cast<uint64_t>(N));
         } else {
           uint32_t bits;
           const float4 e4 = tab[static_cast<size_t>(i)];
@@ -862,7 +881,13 @@ static int create_plan(cmb3d_plan_t* out, int method, int N, int M, int h, doubl
           std::memcpy(&sgn, &e4.z, sizeof(sgn));
           const uint64_t by = (bits >> 11) & 2047u, bz = (bits >> 22) | ((sgn >> 31) << 10);
           key = bz * static_cast<uint64_t>(N) + by;
+          bx = static_cast<int>(bits & 2047u);
         }
+        if (key != prev && prev != ~uint64_t(0)) {
+          flush(prev);
+          cur = 0;
+        }
+        for (int a = 0; a < K; ++a) cur |= 1u << (((bx + a + OFF + N) & (N - 1)) >> csh);
         if (key == prev) continue;
         prev = key;
         const int bz = static_cast<int>(key / static_cast<uint64_t>(N)), by = static_cast<int>(key % N);
@@ -874,6 +899,7 @@ static int create_plan(cmb3d_plan_t* out, int method, int N, int M, int h, doubl
           }
         }
       }
+      if (prev != ~uint64_t(0)) flush(prev);
       for (int z = 0; z < N; ++z) {
         bool any = false;
         for (int w = 0; w < N / 32; ++w) {
@@ -890,7 +916,14 @@ static int create_plan(cmb3d_plan_t* out, int method, int N, int M, int h, doubl
         rowmask.clear();
       } else {
         while (rows.size() % cmb3d::kRowListPad) rows.push_back(nz * N);   // scratch row past the box
+        rowcols.resize(rows.size());
+        for (size_t k = 0; k < rows.size(); ++k) {
+          rowcols[k] = rows[k] < nz * N ? colmask[static_cast<size_t>(rows[k])] : 0u;   // scratch: store nothing
+          x_stored += static_cast<int64_t>(__builtin_popcount(rowcols[k])) * (N / 32);
+        }
       }
+      colmask.clear();
+      colmask.shrink_to_fit();
     }
     if (method == 2) {                                // every layer and row, for whole layers
       for (int z = 0; z < h; ++z) planes_all.push_back(z);
@@ -930,6 +963,7 @@ static int create_plan(cmb3d_plan_t* out, int method, int N, int M, int h, doubl
       (!rows.empty() && ((st = dev_alloc(p, &p->d_rows, rows.size(), "row list")) != CMB3D_OK ||
                          (st = dev_alloc(p, &p->d_planes, planes.size(), "plane list")) != CMB3D_OK ||
                          (st = dev_alloc(p, &p->d_rowmask, rowmask.size(), "row mask")) != CMB3D_OK ||
+                         (st = dev_alloc(p, &p->d_rowcols, rowcols.size(), "row column blocks")) != CMB3D_OK ||
                          (st = dev_alloc(p, &p->d_zmask, static_cast<size_t>((N + 31) / 32), "plane mask")) != CMB3D_OK))) {
     free_plan(p);
     return st;
@@ -956,6 +990,8 @@ static int create_plan(cmb3d_plan_t* out, int method, int N, int M, int h, doubl
       e = cudaMemcpy(p->d_planes, planes.data(), planes.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
       e = cudaMemcpy(p->d_rowmask, rowmask.data(), rowmask.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(p->d_rowcols, rowcols.data(), rowcols.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
       std::vector<uint32_t> zmask(static_cast<size_t>((N + 31) / 32), 0u);
       for (int32_t z : planes) zmask[static_cast<size_t>(z) >> 5] |= 1u << (z & 31);
@@ -968,6 +1004,7 @@ static int create_plan(cmb3d_plan_t* out, int method, int N, int M, int h, doubl
     p->prune = true;
     p->nplanes = static_cast<int64_t>(planes.size());
     p->nrows_pad = static_cast<int64_t>(rows.size());
+    p->x_stored = x_stored;
     p->nrows = 0;
     for (int32_t rr : rows) p->nrows += rr < nz * N ? 1 : 0;
   }
@@ -1506,7 +1543,8 @@ int batch_streams(const cmb3d_plan_t* plans, const uint64_t* seeds, float* const
             el = yv == gemm_y_variant(N) ? launch_y(p, yv, bc.cap2)
                                          : cmb3d::launch_yfft(N, yv, p->buf, p->tw, bc.cap2, p->d_planes,
                                                               static_cast<int>(p->nplanes), p->d_rowmask);
-            if (el == cudaSuccess) el = cmb3d::launch_xc2r(N, xv, p->buf, p->tw, bc.cap2, p->d_rows, p->nrows_pad);
+            if (el == cudaSuccess)
+              el = cmb3d::launch_xc2r(N, xv, p->buf, p->tw, bc.cap2, p->d_rows, p->nrows_pad, p->d_rowcols);
           } else if (sc.fused >= 0) {
             el = cmb3d::launch_yx_fused(N, sc.fused, p->buf, p->tw, bc.cap2);
           } else {
@@ -1603,6 +1641,7 @@ int batch_persistent(const cmb3d_plan_t* plans, const uint64_t* seeds, float* co
     bb.planes = p->prune ? p->d_planes : nullptr;
     bb.rowmask = p->prune ? p->d_rowmask : nullptr;
     bb.rows = p->prune ? p->d_rows : nullptr;
+    bb.cols = p->prune ? p->d_rowcols : nullptr;
     bb.zmask = p->prune && p->zhi == 0 ? p->d_zmask : nullptr;
     bb.zlo = p->prune ? p->zlo : 0;
     bb.zhi = p->prune && p->zhi > 0 ? p->zhi : N;
@@ -1796,6 +1835,13 @@ int cmb3d_plan_prune_info(cmb3d_plan_t p, int64_t* planes, int64_t* rows) {
   const int nz = p->method == 2 ? p->h : p->N;
   if (planes) *planes = p->prune ? p->nplanes : nz;
   if (rows) *rows = p->prune ? p->nrows : static_cast<int64_t>(nz) * p->N;
+  return CMB3D_OK;
+}
+
+int cmb3d_plan_x_stored(cmb3d_plan_t p, int64_t* reals) {
+  if (!p || !reals) return fail(CMB3D_EINVAL, "plan or reals is NULL");
+  const int nz = p->method == 2 ? p->h : p->N;
+  *reals = p->prune ? p->x_stored : static_cast<int64_t>(nz) * p->N * p->N;
   return CMB3D_OK;
 }
 

@@ -44,6 +44,18 @@ def stencil_rows(pix, N, L, r, interp):
     return rows
 
 
+def stored_reals(pix, N, L, r, interp):
+    """Reals the pruned x pass stores: per (z, y) row, every block of N/32
+    columns holding an x that a stencil on that row reads (oracle cells)."""
+    b, _ = orc.pixel_cells(pix, N, L, r)
+    offs = np.array((-1, 0, 1, 2) if interp == 3 else (0, 1))
+    z = (b[:, 2][:, None, None, None] + offs[:, None, None]) % N
+    y = (b[:, 1][:, None, None, None] + offs[None, :, None]) % N
+    x = (b[:, 0][:, None, None, None] + offs[None, None, :]) % N
+    rowblk = (z * N + y) * 32 + x // (N // 32)
+    return len(np.unique(rowblk)) * (N // 32)
+
+
 @pytest.mark.parametrize("N,nside,fsky,interp,flags", [
     (128, 128, 0.4, 3, 0),
     (256, 256, 0.3, 3, 0),
@@ -64,6 +76,10 @@ def test_pruned_map_equals_whole_box_map(N, nside, fsky, interp, flags):
         assert cmb3d.cmb3d_plan_prune_info(pruned.handle) == (len(planes), len(rows))
         assert cmb3d.cmb3d_plan_prune_info(whole.handle) == (N, N * N)
         assert len(rows) < 0.5 * N * N
+        # the x pass writes back only the column blocks the stencils read
+        assert cmb3d.cmb3d_plan_x_stored(pruned.handle) == stored_reals(pix, N, L, 1.0, interp)
+        assert cmb3d.cmb3d_plan_x_stored(whole.handle) == N ** 3
+        assert cmb3d.cmb3d_plan_x_stored(pruned.handle) < 0.5 * len(rows) * N
         for seed in (0, 9):
             a = pruned.realize_sample(seed).cpu().numpy()
             b = whole.realize_sample(seed).cpu().numpy()
