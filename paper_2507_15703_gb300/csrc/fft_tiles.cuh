@@ -173,12 +173,13 @@ __device__ __forceinline__ void draw_zfft_tile(float2* __restrict__ buf, const f
     col = buf + static_cast<size_t>(my) * N2 + xp;
   }
   // The thread's outputs are n = j + k NB for k < R (in the engine's output
-  // order), so the stored range zlo <= n < zhi is one run of k.  From radix 16
-  // one mask per thread replaces two compares per output (measured: fewer
-  // lane-instructions at radix 16, more at radix 8, where a thread has only
-  // eight outputs to spread the mask over).
+  // order), so the stored range zlo <= n < zhi is one run of k.  At radix 16
+  // up to N = 1024 one mask per thread replaces two compares per output
+  // (measured: 1.8 % faster at 1024^3; slower at radix 8, where a thread has
+  // only eight outputs to spread the mask over, and at 2048^3).
+  constexpr bool kMask = R >= 16 && N <= 1024;
   uint32_t kmask = 0u;
-  if constexpr (R >= 16) {
+  if constexpr (kMask) {
     const int klo = min(R, max(0, (zlo - j + NB - 1) / NB)), khi = min(R, max(0, (zhi - j + NB - 1) / NB));
     kmask = store ? (((1u << khi) - 1u) & ~((1u << klo) - 1u)) : 0u;
   }
@@ -186,7 +187,7 @@ __device__ __forceinline__ void draw_zfft_tile(float2* __restrict__ buf, const f
       v, sm, tw, j, [&](int n) { return col_slot<R, T>(n, c); },
       [&](int n, float2 x) {
         bool in_range;
-        if constexpr (R >= 16)
+        if constexpr (kMask)
           in_range = (kmask >> ((n - j) / NB)) & 1u;
         else
           in_range = store && n >= zlo && n < zhi;
