@@ -1,7 +1,7 @@
 """What the learned inversion gains over the method without it.
 
 The MLP (trained here on the GPU by the library's own kernels, label-free
-through the forward relation) is judged on held-out spectra of the family
+through the forward relation) is evaluated on held-out spectra of the family
 against the library's NNLS inversion on the same k nodes.  Alone, its
 forward-projected C_l error stays within 1.5x of the NNLS optimum at a
 thousandth of the time.  Refined on the GPU by accelerated projected gradient
