@@ -467,7 +467,7 @@ def secondary_figure(args, dev, stream, seed0, maps=50):
 
 
 def train_learned_inversion(args, w, dev):
-    """Train the MLP inversion on the GPU (own kernels) and judge it against
+    """Train the MLP inversion on the GPU (own kernels) and compare it with
     the library's NNLS inversion on held-out spectra of the same family."""
     import torch
     from paper_2507_15703_gb300 import cmb3d
