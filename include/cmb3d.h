@@ -593,6 +593,18 @@ int cmb3d_plan_prune_info(cmb3d_plan_t plan, int64_t* planes, int64_t* rows);
  */
 int cmb3d_plan_x_stored(cmb3d_plan_t plan, int64_t* reals);
 
+/*
+ * Host-only (no device, no allocation on any GPU): the extents a 3-D plan with
+ * the same arguments would build from its pixels, counts[0..3] = z-planes the
+ * y pass covers, (z, y) rows the x pass covers, reals the x pass stores, and
+ * gather runs (pixels of one base cell, at most 8 per run; 0 with
+ * CMB3D_FLAG_NO_SORT).  Without pruning (CMB3D_FLAG_NO_PRUNE, N < 128, or
+ * stencils on every row) N, N^2 and N^3.  Arguments and their checks as for
+ * cmb3d_plan; counts: host array of 4.
+ */
+int cmb3d_pixel_tables_host(int N, double L, double r, const double* pix_xyz, int64_t npix, int interp,
+                            uint32_t flags, int64_t* counts);
+
 /* Release the plan and all device memory it owns (NULL is ignored). */
 void cmb3d_destroy(cmb3d_plan_t plan);
 

@@ -85,6 +85,8 @@ PROTOTYPES = {
     "cmb3d_plan_info": (_i32, [_vp, C.POINTER(_i32), C.POINTER(_i64), C.POINTER(_i64)]),
     "cmb3d_plan_prune_info": (_i32, [_vp, C.POINTER(_i64), C.POINTER(_i64)]),
     "cmb3d_plan_x_stored": (_i32, [_vp, C.POINTER(_i64)]),
+    "cmb3d_pixel_tables_host": (_i32, [_i32, C.c_double, C.c_double, C.c_void_p, _i64, _i32, C.c_uint32,
+                                       C.POINTER(_i64)]),
     "cmb3d_plan_schedule": (_i32, [_vp, C.POINTER(_i32)]),
     "cmb3d_batch_schedule": (_i32, [_vp, C.POINTER(_i32), C.POINTER(_i32)]),
     "cmb3d_plan_set_schedule": (_i32, [_vp, C.POINTER(_i32)]),
@@ -384,6 +386,18 @@ def cmb3d_plan_info(plan: int) -> tuple[int, int, int]:
     n, npix, nbytes = _i32(), _i64(), _i64()
     _check(lib.cmb3d_plan_info(plan, C.byref(n), C.byref(npix), C.byref(nbytes)), "cmb3d_plan_info")
     return n.value, npix.value, nbytes.value
+
+
+def cmb3d_pixel_tables_host(N: int, L: float, r: float, pix_xyz, interp: int, flags: int = 0) -> tuple:
+    """(z-planes, rows, stored x reals, gather runs) a 3-D plan with these
+    arguments would build; host only."""
+    import numpy as np
+    lib = load()
+    pix = np.ascontiguousarray(pix_xyz, dtype=np.float64).reshape(-1, 3)
+    out = (_i64 * 4)()
+    _check(lib.cmb3d_pixel_tables_host(int(N), float(L), float(r), pix.ctypes.data if pix.size else None,
+                                       int(pix.shape[0]), int(interp), int(flags), out), "cmb3d_pixel_tables_host")
+    return tuple(int(v) for v in out)
 
 
 def cmb3d_plan_x_stored(plan: int) -> int:

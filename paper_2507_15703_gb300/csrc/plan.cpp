@@ -579,6 +579,176 @@ int run_map_pipelined(cmb3d_plan_s* p, uint64_t seed, float* out, cudaStream_t s
   return CMB3D_OK;
 }
 
+// Host tables of a plan, built from the pixels alone (no device): the pixel
+// table in gather order and its permutation, the gather runs, and the pruned
+// transform's row mask, plane and row lists and per-row column blocks.
+// Throws std::bad_alloc.
+struct PixelTables {
+  std::vector<float4> tab;
+  std::vector<int32_t> perm;
+  std::vector<uint32_t> rowmask;
+  std::vector<int32_t> planes, rows, planes_all, rows_all;
+  std::vector<int2> runs;
+  std::vector<uint32_t> rowcols;   // per listed row: the column blocks (N/32 columns) the stencils read
+  int64_t x_stored = 0;            // reals the pruned x pass stores
+  bool outside = false;            // 2-D: a stencil leaves the layers
+};
+
+void build_pixel_tables(int N, int nz, int method, int h, double L, double r, double z0, const double* pix_xyz,
+                        int64_t npix, int interp, uint32_t flags, PixelTables* t) {
+  std::vector<float4>& tab = t->tab;
+  std::vector<int32_t>& perm = t->perm;
+  std::vector<uint32_t>& rowmask = t->rowmask;
+  std::vector<int32_t>& planes = t->planes;
+  std::vector<int32_t>& rows = t->rows;
+  std::vector<int32_t>& planes_all = t->planes_all;
+  std::vector<int32_t>& rows_all = t->rows_all;
+  std::vector<int2>& runs = t->runs;
+  std::vector<uint32_t>& rowcols = t->rowcols;
+  std::vector<uint32_t> colmask;
+  int64_t& x_stored = t->x_stored;
+  bool& outside = t->outside;
+  tab.resize(static_cast<size_t>(npix));
+  std::vector<std::pair<uint64_t, int32_t>> order;
+  const bool sort = !(flags & CMB3D_FLAG_NO_SORT);
+  if (sort) order.resize(static_cast<size_t>(npix));
+  const double dp = L / N;
+  const double half_l = 0.5 * L;
+  std::vector<float4> raw(static_cast<size_t>(npix));
+  for (int64_t i = 0; i < npix; ++i) {
+    uint32_t b[3];
+    float t[3];
+    for (int a = 0; a < 3; ++a) {
+      const double u = (r * pix_xyz[3 * i + a] + (method == 2 && a == 2 ? -z0 : half_l)) / dp;
+      const double fl = std::floor(u);
+      const double frac = u - fl;
+      int64_t bi;
+      if (method == 2 && a == 2) {                  // layers: no wrap, whole stencil inside
+        bi = fl >= -2.0 && fl <= 2048.0 ? static_cast<int64_t>(fl) : -8;
+        const int64_t lo = interp == CMB3D_TRICUBIC ? bi - 1 : bi, hi = interp == CMB3D_TRICUBIC ? bi + 2 : bi + 1;
+        if (lo < 0 || hi > h - 1) {
+          outside = true;
+          bi = 0;
+        }
+      } else {
+        bi = static_cast<int64_t>(fl) % N;
+        if (bi < 0) bi += N;
+      }
+      b[a] = static_cast<uint32_t>(bi);
+      t[a] = static_cast<float>(frac);
+    }
+    float tz = t[2];
+    if (b[2] & 1024u) tz = -tz;  // bit 10 of bz rides in the sign of tz (tz >= 0, -0.0f included)
+    uint32_t packed = cmb3d::pack_cell(b[0], b[1], b[2]);
+    float w;
+    std::memcpy(&w, &packed, sizeof(w));
+    raw[static_cast<size_t>(i)] = make_float4(t[0], t[1], tz, w);
+    if (sort)
+      order[static_cast<size_t>(i)] = {(static_cast<uint64_t>(b[2]) * N + b[1]) * N + b[0], static_cast<int32_t>(i)};
+  }
+  if (sort) {
+    std::sort(order.begin(), order.end());
+    perm.resize(static_cast<size_t>(npix));
+    for (int64_t i = 0; i < npix; ++i) {
+      perm[static_cast<size_t>(i)] = order[static_cast<size_t>(i)].second;
+      tab[static_cast<size_t>(i)] = raw[static_cast<size_t>(order[static_cast<size_t>(i)].second)];
+    }
+    // runs of at most kGatherRun pixels sharing one base cell (the key is the cell)
+    for (int64_t i = 0; i < npix;) {
+      int64_t j = i + 1;
+      while (j < npix && j - i < cmb3d::kGatherRun &&
+             order[static_cast<size_t>(j)].first == order[static_cast<size_t>(i)].first)
+        ++j;
+      runs.push_back(make_int2(static_cast<int>(i), static_cast<int>(j - i)));
+      i = j;
+    }
+  } else {
+    tab.swap(raw);
+  }
+  // rows (z, y) read by the interpolation stencils: z in bz + OFF .. bz + OFF + K - 1
+  // (mod N), likewise y; consecutive pixels of one row are visited once
+  const int K = interp == CMB3D_TRICUBIC ? 4 : 2, OFF = interp == CMB3D_TRICUBIC ? -1 : 0;
+  const size_t words = static_cast<size_t>(N) * N / 32;
+  if (!(flags & CMB3D_FLAG_NO_PRUNE) && N >= 128 && npix > 0) {
+    rowmask.assign(words, 0u);
+    colmask.assign(static_cast<size_t>(nz) * N, 0u);
+    const int csh = cmb3d::ilog2i(N) - 5;            // column block: N / 32 columns
+    uint64_t prev = ~uint64_t(0);
+    uint32_t cur = 0;                               // column blocks of the current (z, y) group
+    auto flush = [&](uint64_t key) {
+      const int bz = static_cast<int>(key / static_cast<uint64_t>(N)), by = static_cast<int>(key % N);
+      for (int c = 0; c < K; ++c) {
+        const int z = (bz + c + OFF + N) & (N - 1);
+        if (z >= nz) continue;
+        for (int b = 0; b < K; ++b)
+          colmask[static_cast<size_t>(z) * N + static_cast<size_t>((by + b + OFF + N) & (N - 1))] |= cur;
+      }
+    };
+    for (int64_t i = 0; i < npix; ++i) {
+      uint64_t key;
+      int bx;
+      if (sort) {
+        key = order[static_cast<size_t>(i)].first / static_cast<uint64_t>(N);
+        bx = static_cast<int>(order[static_cast<size_t>(i)].first % static_cast<uint64_t>(N));
+      } else {
+        uint32_t bits;
+        const float4 e4 = tab[static_cast<size_t>(i)];
+        std::memcpy(&bits, &e4.w, sizeof(bits));
+        uint32_t sgn;
+        std::memcpy(&sgn, &e4.z, sizeof(sgn));
+        const uint64_t by = (bits >> 11) & 2047u, bz = (bits >> 22) | ((sgn >> 31) << 10);
+        key = bz * static_cast<uint64_t>(N) + by;
+        bx = static_cast<int>(bits & 2047u);
+      }
+      if (key != prev && prev != ~uint64_t(0)) {
+        flush(prev);
+        cur = 0;
+      }
+      for (int a = 0; a < K; ++a) cur |= 1u << (((bx + a + OFF + N) & (N - 1)) >> csh);
+      if (key == prev) continue;
+      prev = key;
+      const int bz = static_cast<int>(key / static_cast<uint64_t>(N)), by = static_cast<int>(key % N);
+      for (int c = 0; c < K; ++c) {
+        const int z = (bz + c + OFF + N) & (N - 1);
+        for (int b = 0; b < K; ++b) {
+          const size_t row = static_cast<size_t>(z) * N + static_cast<size_t>((by + b + OFF + N) & (N - 1));
+          rowmask[row >> 5] |= 1u << (row & 31);
+        }
+      }
+    }
+    if (prev != ~uint64_t(0)) flush(prev);
+    for (int z = 0; z < N; ++z) {
+      bool any = false;
+      for (int w = 0; w < N / 32; ++w) {
+        const uint32_t m = rowmask[static_cast<size_t>(z) * (N / 32) + w];
+        any = any || m != 0;
+        for (int bit = 0; bit < 32; ++bit)
+          if ((m >> bit) & 1u) rows.push_back(z * N + w * 32 + bit);
+      }
+      if (any) planes.push_back(z);
+    }
+    if (static_cast<int64_t>(rows.size()) == static_cast<int64_t>(nz) * N) {   // nothing to prune
+      rows.clear();
+      planes.clear();
+      rowmask.clear();
+    } else {
+      while (rows.size() % cmb3d::kRowListPad) rows.push_back(nz * N);   // scratch row past the box
+      rowcols.resize(rows.size());
+      for (size_t k = 0; k < rows.size(); ++k) {
+        rowcols[k] = rows[k] < nz * N ? colmask[static_cast<size_t>(rows[k])] : 0u;   // scratch: store nothing
+        x_stored += static_cast<int64_t>(__builtin_popcount(rowcols[k])) * (N / 32);
+      }
+    }
+    colmask.clear();
+    colmask.shrink_to_fit();
+  }
+  if (method == 2) {                                // every layer and row, for whole layers
+    for (int z = 0; z < h; ++z) planes_all.push_back(z);
+    for (int rr = 0; rr < h * N; ++rr) rows_all.push_back(rr);
+    while (rows_all.size() % cmb3d::kRowListPadAny) rows_all.push_back(h * N);
+  }
+}
+
 int check_ready(cmb3d_plan_s* p) {
   if (!p) return fail(CMB3D_EINVAL, "plan is NULL");
   if (!p->has_spec) return fail(CMB3D_ENOSPEC, "cmb3d_set_spectrum has not been called on this plan");
@@ -782,158 +952,24 @@ static int create_plan(cmb3d_plan_t* out, int method, int N, int M, int h, doubl
   }
 
   // ---- pixel table (FP64 mapping, then FP32 fractions) --------------------
-  std::vector<float4> tab;
-  std::vector<int32_t> perm;
-  std::vector<uint32_t> rowmask;
-  std::vector<int32_t> planes, rows, planes_all, rows_all;
-  std::vector<int2> runs;
-  std::vector<uint32_t> colmask, rowcols;           // column blocks the stencils read, per row / per listed row
-  int64_t x_stored = 0;
-  bool outside = false;                               // 2-D: a stencil leaves the layers
+  PixelTables pt;
   try {
-    tab.resize(static_cast<size_t>(npix));
-    std::vector<std::pair<uint64_t, int32_t>> order;
-    const bool sort = !(flags & CMB3D_FLAG_NO_SORT);
-    if (sort) order.resize(static_cast<size_t>(npix));
-    const double dp = L / N;
-    const double half_l = 0.5 * L;
-    std::vector<float4> raw(static_cast<size_t>(npix));
-    for (int64_t i = 0; i < npix; ++i) {
-      uint32_t b[3];
-      float t[3];
-      for (int a = 0; a < 3; ++a) {
-        const double u = (r * pix_xyz[3 * i + a] + (method == 2 && a == 2 ? -z0 : half_l)) / dp;
-        const double fl = std::floor(u);
-        const double frac = u - fl;
-        int64_t bi;
-        if (method == 2 && a == 2) {                  // layers: no wrap, whole stencil inside
-          bi = fl >= -2.0 && fl <= 2048.0 ? static_cast<int64_t>(fl) : -8;
-          const int64_t lo = interp == CMB3D_TRICUBIC ? bi - 1 : bi, hi = interp == CMB3D_TRICUBIC ? bi + 2 : bi + 1;
-          if (lo < 0 || hi > h - 1) {
-            outside = true;
-            bi = 0;
-          }
-        } else {
-          bi = static_cast<int64_t>(fl) % N;
-          if (bi < 0) bi += N;
-        }
-        b[a] = static_cast<uint32_t>(bi);
-        t[a] = static_cast<float>(frac);
-      }
-      float tz = t[2];
-      if (b[2] & 1024u) tz = -tz;  // bit 10 of bz rides in the sign of tz (tz >= 0, -0.0f included)
-      uint32_t packed = cmb3d::pack_cell(b[0], b[1], b[2]);
-      float w;
-      std::memcpy(&w, &packed, sizeof(w));
-      raw[static_cast<size_t>(i)] = make_float4(t[0], t[1], tz, w);
-      if (sort)
-        order[static_cast<size_t>(i)] = {(static_cast<uint64_t>(b[2]) * N + b[1]) * N + b[0], static_cast<int32_t>(i)};
-    }
-    if (sort) {
-      std::sort(order.begin(), order.end());
-      perm.resize(static_cast<size_t>(npix));
-      for (int64_t i = 0; i < npix; ++i) {
-        perm[static_cast<size_t>(i)] = order[static_cast<size_t>(i)].second;
-        tab[static_cast<size_t>(i)] = raw[static_cast<size_t>(order[static_cast<size_t>(i)].second)];
-      }
-      // runs of at most kGatherRun pixels sharing one base cell (the key is the cell)
-      for (int64_t i = 0; i < npix;) {
-        int64_t j = i + 1;
-        while (j < npix && j - i < cmb3d::kGatherRun &&
-               order[static_cast<size_t>(j)].first == order[static_cast<size_t>(i)].first)
-          ++j;
-        runs.push_back(make_int2(static_cast<int>(i), static_cast<int>(j - i)));
-        i = j;
-      }
-    } else {
-      tab.swap(raw);
-    }
-    // rows (z, y) read by the interpolation stencils: z in bz + OFF .. bz + OFF + K - 1
-    // (mod N), likewise y; consecutive pixels of one row are visited once
-    const int K = interp == CMB3D_TRICUBIC ? 4 : 2, OFF = interp == CMB3D_TRICUBIC ? -1 : 0;
-    const size_t words = static_cast<size_t>(N) * N / 32;
-    if (!(flags & CMB3D_FLAG_NO_PRUNE) && N >= 128 && npix > 0) {
-      rowmask.assign(words, 0u);
-      colmask.assign(static_cast<size_t>(nz) * N, 0u);
-      const int csh = cmb3d::ilog2i(N) - 5;            // column block: N / 32 columns
-      uint64_t prev = ~uint64_t(0);
-      uint32_t cur = 0;                               // column blocks of the current (z, y) group
-      auto flush = [&](uint64_t key) {
-        const int bz = static_cast<int>(key / static_cast<uint64_t>(N)), by = static_cast<int>(key % N);
-        for (int c = 0; c < K; ++c) {
-          const int z = (bz + c + OFF + N) & (N - 1);
-          if (z >= nz) continue;
-          for (int b = 0; b < K; ++b)
-            colmask[static_cast<size_t>(z) * N + static_cast<size_t>((by + b + OFF + N) & (N - 1))] |= cur;
-        }
-      };
-      for (int64_t i = 0; i < npix; ++i) {
-        uint64_t key;
-        int bx;
-        if (sort) {
-          key = order[static_cast<size_t>(i)].first / static_cast<uint64_t>(N);
-          bx = static_cast<int>(order[static_cast<size_t>(i)].first % static_cast<uint64_t>(N));
-        } else {
-          uint32_t bits;
-          const float4 e4 = tab[static_cast<size_t>(i)];
-          std::memcpy(&bits, &e4.w, sizeof(bits));
-          uint32_t sgn;
-          std::memcpy(&sgn, &e4.z, sizeof(sgn));
-          const uint64_t by = (bits >> 11) & 2047u, bz = (bits >> 22) | ((sgn >> 31) << 10);
-          key = bz * static_cast<uint64_t>(N) + by;
-          bx = static_cast<int>(bits & 2047u);
-        }
-        if (key != prev && prev != ~uint64_t(0)) {
-          flush(prev);
-          cur = 0;
-        }
-        for (int a = 0; a < K; ++a) cur |= 1u << (((bx + a + OFF + N) & (N - 1)) >> csh);
-        if (key == prev) continue;
-        prev = key;
-        const int bz = static_cast<int>(key / static_cast<uint64_t>(N)), by = static_cast<int>(key % N);
-        for (int c = 0; c < K; ++c) {
-          const int z = (bz + c + OFF + N) & (N - 1);
-          for (int b = 0; b < K; ++b) {
-            const size_t row = static_cast<size_t>(z) * N + static_cast<size_t>((by + b + OFF + N) & (N - 1));
-            rowmask[row >> 5] |= 1u << (row & 31);
-          }
-        }
-      }
-      if (prev != ~uint64_t(0)) flush(prev);
-      for (int z = 0; z < N; ++z) {
-        bool any = false;
-        for (int w = 0; w < N / 32; ++w) {
-          const uint32_t m = rowmask[static_cast<size_t>(z) * (N / 32) + w];
-          any = any || m != 0;
-          for (int bit = 0; bit < 32; ++bit)
-            if ((m >> bit) & 1u) rows.push_back(z * N + w * 32 + bit);
-        }
-        if (any) planes.push_back(z);
-      }
-      if (static_cast<int64_t>(rows.size()) == static_cast<int64_t>(nz) * N) {   // nothing to prune
-        rows.clear();
-        planes.clear();
-        rowmask.clear();
-      } else {
-        while (rows.size() % cmb3d::kRowListPad) rows.push_back(nz * N);   // scratch row past the box
-        rowcols.resize(rows.size());
-        for (size_t k = 0; k < rows.size(); ++k) {
-          rowcols[k] = rows[k] < nz * N ? colmask[static_cast<size_t>(rows[k])] : 0u;   // scratch: store nothing
-          x_stored += static_cast<int64_t>(__builtin_popcount(rowcols[k])) * (N / 32);
-        }
-      }
-      colmask.clear();
-      colmask.shrink_to_fit();
-    }
-    if (method == 2) {                                // every layer and row, for whole layers
-      for (int z = 0; z < h; ++z) planes_all.push_back(z);
-      for (int rr = 0; rr < h * N; ++rr) rows_all.push_back(rr);
-      while (rows_all.size() % cmb3d::kRowListPadAny) rows_all.push_back(h * N);
-    }
+    build_pixel_tables(N, nz, method, h, L, r, z0, pix_xyz, npix, interp, flags, &pt);
   } catch (const std::bad_alloc&) {
     delete p;
     return fail(CMB3D_ENOMEM, "host allocation of the pixel table");
   }
+  std::vector<float4>& tab = pt.tab;
+  std::vector<int32_t>& perm = pt.perm;
+  std::vector<uint32_t>& rowmask = pt.rowmask;
+  std::vector<int32_t>& planes = pt.planes;
+  std::vector<int32_t>& rows = pt.rows;
+  std::vector<int32_t>& planes_all = pt.planes_all;
+  std::vector<int32_t>& rows_all = pt.rows_all;
+  std::vector<int2>& runs = pt.runs;
+  std::vector<uint32_t>& rowcols = pt.rowcols;
+  const int64_t x_stored = pt.x_stored;
+  const bool outside = pt.outside;
   if (outside) {
     delete p;
     return fail(CMB3D_EINVAL, "a pixel's interpolation stencil leaves the h simulated layers");
@@ -1835,6 +1871,34 @@ int cmb3d_plan_prune_info(cmb3d_plan_t p, int64_t* planes, int64_t* rows) {
   const int nz = p->method == 2 ? p->h : p->N;
   if (planes) *planes = p->prune ? p->nplanes : nz;
   if (rows) *rows = p->prune ? p->nrows : static_cast<int64_t>(nz) * p->N;
+  return CMB3D_OK;
+}
+
+int cmb3d_pixel_tables_host(int N, double L, double r, const double* pix_xyz, int64_t npix, int interp,
+                            uint32_t flags, int64_t* counts) {
+  if (!counts) return fail(CMB3D_EINVAL, "counts is NULL");
+  if (!is_pow2(N) || N < 8 || N > 2048) return fail(CMB3D_EUNSUPPORTED, "N must be a power of two in [8, 2048]");
+  if (!(std::isfinite(L) && L > 0) || !(std::isfinite(r) && r > 0)) return fail(CMB3D_EINVAL, "L and r must be finite and > 0");
+  if (!(L > 2.0 * r) && !(flags & CMB3D_FLAG_ALLOW_WRAP))
+    return fail(CMB3D_EINVAL, "L must exceed 2r (set CMB3D_FLAG_ALLOW_WRAP to allow wrapping)");
+  if (npix < 0 || npix >= (int64_t(1) << 31)) return fail(CMB3D_EINVAL, "npix out of range");
+  if (npix > 0 && !pix_xyz) return fail(CMB3D_EINVAL, "pix_xyz is NULL");
+  if (interp != CMB3D_TRILINEAR && interp != CMB3D_TRICUBIC) return fail(CMB3D_EINVAL, "interp must be 1 or 3");
+  for (int64_t i = 0; i < 3 * npix; ++i)
+    if (!std::isfinite(pix_xyz[i])) return fail(CMB3D_EINVAL, "pixel coordinates must be finite");
+  PixelTables t;
+  try {
+    build_pixel_tables(N, N, 3, 0, L, r, 0.0, pix_xyz, npix, interp, flags, &t);
+  } catch (const std::bad_alloc&) {
+    return fail(CMB3D_ENOMEM, "host allocation of the pixel table");
+  }
+  const bool pruned = !t.rows.empty();
+  int64_t listed = 0;
+  for (int32_t rr : t.rows) listed += rr < N * N ? 1 : 0;
+  counts[0] = pruned ? static_cast<int64_t>(t.planes.size()) : N;
+  counts[1] = pruned ? listed : static_cast<int64_t>(N) * N;
+  counts[2] = pruned ? t.x_stored : static_cast<int64_t>(N) * N * N;
+  counts[3] = static_cast<int64_t>(t.runs.size());
   return CMB3D_OK;
 }
 
