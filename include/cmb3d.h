@@ -594,8 +594,10 @@ int cmb3d_plan_prune_info(cmb3d_plan_t plan, int64_t* planes, int64_t* rows);
 int cmb3d_plan_x_stored(cmb3d_plan_t plan, int64_t* reals);
 
 /*
- * Host-only (no device, no allocation on any GPU): the extents a 3-D plan with
- * the same arguments would build from its pixels, counts[0..3] = z-planes the
+ * Host-only (no device, no allocation on any GPU): the extents of the pruned
+ * transform (the part of the cubic box the cap's pixels read, the GPU form of
+ * the cap-sized box of Sec. II.C) that a 3-D plan with the same arguments
+ * would build from its pixels, counts[0..3] = z-planes the
  * y pass covers, (z, y) rows the x pass covers, reals the x pass stores, and
  * gather runs (pixels of one base cell, at most 8 per run; 0 with
  * CMB3D_FLAG_NO_SORT).  Without pruning (CMB3D_FLAG_NO_PRUNE, N < 128, or
