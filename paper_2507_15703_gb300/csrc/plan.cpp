@@ -15,6 +15,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "internal.h"
 #include "spectrum.h"
@@ -303,9 +304,24 @@ int check_device_error(cmb3d_plan_s* p) {
   return CMB3D_OK;
 }
 
-// Launch `f` on stream s, bracketed by CUDA events when the plan times stages.
+// An NVTX range named after the pass around each launch, for timeline tools
+// (nsys, ncu's NVTX filters); inert when no tool is attached.
+struct NvtxRange {
+  explicit NvtxRange(int stage) {
+    static const char* const kNames[] = {"cmb3d draw+z", "cmb3d y pass", "cmb3d x pass", "cmb3d gather",
+                                         "cmb3d y+x fused"};
+    nvtxRangePushA(stage >= 0 && stage < 5 ? kNames[stage] : "cmb3d pass");
+  }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
+// Launch `f` on stream s inside an NVTX range, bracketed by CUDA events when
+// the plan times stages.
 template <class F>
 cudaError_t timed(cmb3d_plan_s* p, int stage, cudaStream_t s, F f) {
+  NvtxRange range(stage);
   if (!(p->flags & CMB3D_FLAG_STAGE_TIMING) || p->tnext >= kMaxTimingRecs) return f();
   if (p->tnext == p->recs.size()) {
     TimingRec r{stage, nullptr, nullptr};
